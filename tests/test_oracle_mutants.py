@@ -1,0 +1,92 @@
+"""Plant plausible mistakes in a copy of the oracle (on the CPU) and check that the
+pins in test_oracle_pins.py reject every one of them.
+
+Each mutant is oracle.c with one textual change (a dropped term, a wrong bound, a
+flipped comparison, a wrong rounding, a constant typo), compiled into a temporary
+directory and swapped in for the duration of the check.  No mutant can read or
+write out of bounds: each change keeps every index inside the arrays it touches.
+"""
+import os
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as P
+from tests.conftest import read_golden
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+MUTANTS = {
+    "flop drops the row start": ("(int64_t)b_rpt[k + 1] - (int64_t)b_rpt[k]", "(int64_t)b_rpt[k + 1]"),
+    "nnz never deduplicates": ("if (mark[c] != stamp) {", "if (mark[c] != stamp + 1) {"),
+    "marker stamp is the row id": ("int64_t stamp = r; /* unique for this visit */", "int64_t stamp = i;"),
+    "marker stamp never changes": ("int64_t stamp = r; /* unique for this visit */", "int64_t stamp = 0;"),
+    "prediction floors": ("return (a + b - 1) / b;", "return a / b;"),
+    "reference drops M": ("(u128)(uint64_t)z * (u128)(uint64_t)M;", "(u128)(uint64_t)z;"),
+    "reference drops |S|": ("(u128)(uint64_t)F * (u128)(uint64_t)n_ids;", "(u128)(uint64_t)F;"),
+    "sample comparison flipped": ("orc_h32(seed, (uint64_t)i) < threshold", "orc_h32(seed, (uint64_t)i) > threshold"),
+    "hash constant typo": ("0xbf58476d1ce4e5b9ull", "0xbf58476d1ce4e5b8ull"),
+    "draw scales by M/2": ("* (uint64_t)M) >> 32", "* (uint64_t)M) >> 33"),
+    "sample_num rounds up": ("int64_t s = (3 * M) / 1000;", "int64_t s = (3 * M + 999) / 1000;"),
+    "scan subtracts": ("(u128)(uint64_t)f);\n    pred[i] = p;\n    offsets[i + 1] = offsets[i] + p;",
+                       "(u128)(uint64_t)f);\n    pred[i] = p;\n    offsets[i + 1] = offsets[i] - p;"),
+    "empty sample not flagged": ("if (f == 0) status |= ORC_WARN_EMPTY_SAMPLE;", ""),
+    "sampled flop uses first row": ("for (int64_t r = 0; r < n_ids; ++r) f += flop[ids[r]];\n  int64_t status = 0;\n  if (f == 0)",
+                                    "for (int64_t r = 0; r < n_ids; ++r) f += flop[ids[0]];\n  int64_t status = 0;\n  if (f == 0)"),
+}
+
+
+def _pins():
+    g = read_golden
+    yield lambda: P.test_splitmix64_known_answers(g)
+    yield P.test_bernoulli_threshold_extremes
+    yield P.test_bernoulli_membership_matches_hash
+    yield lambda: P.test_paper_sample_num(g)
+    yield P.test_paper_draw_rows_in_range
+    yield lambda: P.test_flop_and_nnz_against_dense_product((17, 33, 9), 0.3)
+    yield lambda: P.test_laplacian_2d_closed_form(9)
+    yield P.test_periodic_laplacian_uniform_rows
+    for name in ("lap64", "er", "rmat", "rect"):
+        yield lambda n=name: P.test_prediction_invariants(n, oracle.BERNOULLI)
+        yield lambda n=name: P.test_prediction_invariants(n, oracle.PAPER_DRAW)
+    yield P.test_empty_sample_falls_back_to_flop
+    yield P.test_paper_draw_counts_repeats
+
+
+@pytest.fixture(scope="module")
+def tmpdir_mod():
+    d = tempfile.mkdtemp(prefix="oracle-mutants-")
+    yield d
+    shutil.rmtree(d, ignore_errors=True)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(name, tmpdir_mod):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name!r} not unique"
+    path_c = os.path.join(tmpdir_mod, f"m{abs(hash(name))}.c")
+    path_so = path_c[:-2] + ".so"
+    with open(path_c, "w") as f:
+        f.write(src.replace(old, new))
+    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", path_c, "-o", path_so], check=True)
+    prev = oracle.use_library(path_so)
+    caught = False
+    try:
+        for pin in _pins():
+            try:
+                pin()
+            except AssertionError:
+                caught = True
+                break
+    finally:
+        oracle.restore_library(prev)
+    assert caught, f"no pin rejects the mutant {name!r}"
+
+
+def test_unmutated_oracle_passes_the_same_pins():
+    for pin in _pins():
+        pin()
