@@ -1,0 +1,190 @@
+/*
+ * spgemm_predict.h - C ABI of a GB300 (sm_103a) library that predicts the output
+ * structure of a sparse matrix product C = A * B with the sampled compression
+ * ratio of Du et al., "Predicting the Output Structure of Sparse Matrix
+ * Multiplication with Sampled Compression Ratio" (arXiv 2207.13848).
+ *
+ * What the library computes (notation of Table I / Sec. II-A: A is M x K, B is
+ * K x N):
+ *   flop_i  number of intermediate products of output row i (Algorithm 1, Sec. V-A)
+ *   F       FLOP(C) = sum of flop_i
+ *   S       a seed-determined sample of A's rows (Sec. IV-A)
+ *   f*, z*  FLOP and exact NNZ of the sampled output rows (Sec. IV-B, IV-D;
+ *           sample_flop and sample_nnz of Algorithm 2, Sec. V-B)
+ *   r*      f* / z*, the sampled compression ratio (Eq. 4)
+ *   pred_i  ceil(flop_i / r*) = ceil(flop_i * z* / f*): the predicted nnz of row i
+ *           (Eq. 4: the FLOP per output row divided by the predicted ratio)
+ *   offsets exclusive prefix sum of pred (M + 1 entries): allocation offsets of C
+ *
+ * Conventions for every entry point:
+ *   - Matrices, outputs, the result record and the workspace live in DEVICE
+ *     memory owned by the caller.  The library allocates nothing and never
+ *     synchronises the device; all work is queued on `stream` (a cudaStream_t
+ *     passed as void*, NULL = the legacy default stream) and is complete when the
+ *     stream reaches that point.
+ *   - The return value reports errors found on the host before anything is
+ *     queued (negative SPGEMM_ERR_* codes; nothing was launched).  Outcomes found
+ *     on the device are written to res->status as SPGEMM_STATUS_* bits.
+ *   - All counts are exact integers; results do not depend on launch shape,
+ *     thread scheduling or the GPU model.
+ *   - The workspace must be zero-filled before its first use and is left
+ *     reusable by every call that ends with a status free of SPGEMM_STATUS_ERR_*
+ *     bits; after such an error, zero it again.  Calls that share one workspace
+ *     must not overlap in time (queue them on one stream).
+ */
+#ifndef SPGEMM_PREDICT_H
+#define SPGEMM_PREDICT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- host return codes ------------------------------------------------------ */
+#define SPGEMM_OK 0
+#define SPGEMM_ERR_INVALID_ARG (-1)  /* null pointer, negative size, bad mode or threshold */
+#define SPGEMM_ERR_DIM_MISMATCH (-2) /* A.cols != B.rows */
+#define SPGEMM_ERR_WORKSPACE (-3)    /* ws_bytes < spgemm_workspace_size(A, B) */
+#define SPGEMM_ERR_CUDA (-4)         /* a CUDA launch or query failed */
+#define SPGEMM_ERR_TOO_LARGE (-5)    /* a size does not fit the int32 index range */
+
+/* ---- device status bits (res->status) ------------------------------------------ */
+#define SPGEMM_STATUS_OK 0
+/* f* = 0 (empty sample, or only product-free rows sampled): the compression
+ * ratio is undefined, so pred_i = flop_i (the upper-bound method of Sec. I).  For
+ * the reference design: |S| = 0, same fallback. */
+#define SPGEMM_STATUS_WARN_EMPTY_SAMPLE 0x1
+/* reference design only: some pred_i exceeded 2^31 - 1 and was saturated. */
+#define SPGEMM_STATUS_WARN_SATURATED 0x2
+/* a column id or row offset outside its valid range was met; the offending terms
+ * were counted as zero (no out-of-bounds access is made).  Results are invalid. */
+#define SPGEMM_STATUS_ERR_BAD_INPUT 0x100
+/* a bounded wait between thread blocks gave up (about one second); results are
+ * invalid and the workspace must be zeroed again. */
+#define SPGEMM_STATUS_ERR_TIMEOUT 0x200
+/* validation only: some row is not strictly increasing (unsorted or repeated
+ * column ids).  The predictor needs unique ids per row; order is free. */
+#define SPGEMM_STATUS_WARN_UNSORTED 0x4
+
+/* ---- types -------------------------------------------------------------------- */
+
+/* CSR matrix (Sec. II-B): row offsets rpt[rows + 1] and column ids col[nnz],
+ * int32, device memory, caller-owned.  Requirements: rpt[0] = 0, rpt
+ * non-decreasing, rpt[rows] = nnz, 0 <= col < cols, ids unique within a row.
+ * Values are never read: the method counts structural products and nonzeros. */
+typedef struct spgemm_csr {
+  int64_t rows;
+  int64_t cols;
+  int64_t nnz;
+  const int32_t* rpt;
+  const int32_t* col;
+} spgemm_csr_t;
+
+/* Row sampling (Sec. IV-A).  h32(seed, x) is the high 32 bits of output x + 1 of
+ * SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) started at state `seed`. */
+#define SPGEMM_SAMPLE_BERNOULLI 0  /* row i is in S iff h32(seed, i) < threshold */
+#define SPGEMM_SAMPLE_PAPER_DRAW 1 /* Algorithm 2: draw r = 0..sample_num-1 picks row
+                                      (h32(seed, r) * M) >> 32, with replacement;
+                                      repeats count with multiplicity */
+
+typedef struct spgemm_config {
+  int32_t mode;        /* SPGEMM_SAMPLE_* */
+  int32_t reserved0;   /* must be 0 */
+  uint64_t threshold;  /* BERNOULLI: in [0, 2^32]; sampling ratio = threshold / 2^32;
+                          2^32 samples every row */
+  int64_t sample_num;  /* PAPER_DRAW: number of draws; 0 selects the paper's rule
+                          min(floor(0.003 M), 300), at least 1 (Algorithm 2) */
+  uint64_t seed;
+} spgemm_config_t;
+
+/* Scalars of one call, written to device memory at the end of the call. */
+typedef struct spgemm_result {
+  int64_t flop_total; /* F (0 where the call does not compute it) */
+  int64_t flop_s;     /* f* */
+  int64_t nnz_s;      /* z* */
+  int64_t n_sampled;  /* |S| */
+  int64_t pred_total; /* offsets[M] */
+  int32_t status;     /* SPGEMM_STATUS_* bits */
+  int32_t reserved;
+} spgemm_result_t;
+
+/* ---- entry points ----------------------------------------------------------------- */
+
+/* Bytes of device workspace every entry point below needs for these operands
+ * (about 8 * A.rows bytes plus a fixed 320 KB).  B may be NULL for
+ * spgemm_sample_rows / spgemm_validate_csr. */
+size_t spgemm_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B);
+
+/* Algorithm 1 (Sec. V-A): flop_row[i] = sum over j in row i of A of
+ * (B.rpt[A.col[j] + 1] - B.rpt[A.col[j]]), int32[A.rows]; res->flop_total = F.
+ * flop_i < 2^31 always holds for valid inputs (flop_i <= nnz(B)). */
+int spgemm_flop_per_row(const spgemm_csr_t* A, const spgemm_csr_t* B, int32_t* flop_row,
+                        spgemm_result_t* res, void* ws, size_t ws_bytes, void* stream);
+
+/* Steps a1-a4: draw the sample S, compute f* and z* (exact nnz of each sampled row
+ * by deduplicating its products, Algorithm 2's hash loop), |S|.  r* = f* / z* is
+ * the predicted compression ratio (Eq. 4).  res->flop_total is not computed (0). */
+int spgemm_predict_cr(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_config_t* cfg,
+                      spgemm_result_t* res, void* ws, size_t ws_bytes, void* stream);
+
+/* The proposed method end to end (Eq. 4, Algorithm 2): f*, z* as in
+ * spgemm_predict_cr, then pred_row[i] = ceil(flop_i * z* / f*) (int32[A.rows]) and
+ * offsets = exclusive scan of pred_row (int64[A.rows + 1]).  flop_row
+ * (int32[A.rows]) receives flop_i when not NULL.  res: F, f*, z*, |S|,
+ * pred_total = offsets[M]; Z2* = F * z* / f*. */
+int spgemm_predict_structure(const spgemm_csr_t* A, const spgemm_csr_t* B,
+                             const spgemm_config_t* cfg, int32_t* pred_row, int64_t* offsets,
+                             int32_t* flop_row, spgemm_result_t* res, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/* The reference design of the prior sampling method (Sec. IV-C, Eq. 2): on the
+ * same sample, Z1* = z* / p with p = |S| / M, CR1 = F / Z1*, and
+ * pred_row[i] = ceil(flop_i * z* * M / (F * |S|)), saturated at 2^31 - 1;
+ * offsets and flop_row as above. */
+int spgemm_predict_reference(const spgemm_csr_t* A, const spgemm_csr_t* B,
+                             const spgemm_config_t* cfg, int32_t* pred_row, int64_t* offsets,
+                             int32_t* flop_row, spgemm_result_t* res, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/* The precise method (symbolic phase, Sec. I), used as ground truth and as the
+ * timed comparison: nnz_row[i] = exact nnz of output row i (int32[A.rows]),
+ * offsets = exclusive scan (int64[A.rows + 1]); res->flop_total = F,
+ * res->pred_total = NNZ(C). */
+int spgemm_symbolic_exact(const spgemm_csr_t* A, const spgemm_csr_t* B, int32_t* nnz_row,
+                          int64_t* offsets, spgemm_result_t* res, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/* The sample S alone (Sec. IV-A): ids[0..|S|) in ascending row order (BERNOULLI)
+ * or draw order (PAPER_DRAW); entries past |S| are untouched.  `capacity` is the
+ * length of ids; |S| > capacity is a host error when it can be known on the host
+ * (PAPER_DRAW) and is otherwise clipped, with res->n_sampled still the full |S|. */
+int spgemm_sample_rows(int64_t rows, const spgemm_config_t* cfg, int32_t* ids, int64_t capacity,
+                       spgemm_result_t* res, void* ws, size_t ws_bytes, void* stream);
+
+/* Device-side check of the CSR requirements above.  res->status receives
+ * SPGEMM_STATUS_ERR_BAD_INPUT (offsets or ids out of range) and/or
+ * SPGEMM_STATUS_WARN_UNSORTED (a row not strictly increasing). */
+int spgemm_validate_csr(const spgemm_csr_t* A, spgemm_result_t* res, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/* Profiling hook (a library utility; the paper has no counterpart).  When
+ * `before` and `after` are non-NULL cudaEvent_t handles (passed as void*), every
+ * later call of spgemm_predict_structure, spgemm_predict_reference,
+ * spgemm_flop_per_row and spgemm_symbolic_exact records `before` on its stream
+ * just before the launch of its main kernel (the fused FLOP/prediction/scan
+ * kernel; for the symbolic phase, the deduplication of all rows) and `after`
+ * just after it, so cudaEventElapsedTime gives that kernel's duration.  Passing
+ * NULL, NULL turns the hook off.  The setting is process-wide; it is meant for
+ * benchmarks, not for concurrent use from several threads.  Returns SPGEMM_OK. */
+int spgemm_set_profile_events(void* before, void* after);
+
+/* Static description of a host return code or of a status bit set. */
+const char* spgemm_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPGEMM_PREDICT_H */

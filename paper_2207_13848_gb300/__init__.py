@@ -1,0 +1,329 @@
+"""GB300 output-structure predictor for SpGEMM C = A*B (sampled compression ratio,
+Du et al., arXiv 2207.13848).
+
+A thin binding over the C ABI declared in ``include/spgemm_predict.h``: the
+functions named ``spgemm_*`` take the same arguments as their C counterparts,
+with torch CUDA tensors standing in for device pointers, and return the C return
+code.  Every step of the computation runs in the CUDA library; importing this
+package does not load it, but the first call does, and fails loudly when the
+library has not been built (``paper_2207_13848_gb300.build.build()``) or no GPU
+is present.  PyTorch is used for device memory and streams only.
+
+Convenience wrappers (``DeviceCSR``, ``Workspace``, ``predict_structure`` ...)
+allocate the outputs with torch and call the C ABI.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+from . import build as _build
+
+# ---- constants mirrored from the header --------------------------------------
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_DIM_MISMATCH = -2
+ERR_WORKSPACE = -3
+ERR_CUDA = -4
+ERR_TOO_LARGE = -5
+STATUS_WARN_EMPTY_SAMPLE = 0x1
+STATUS_WARN_SATURATED = 0x2
+STATUS_WARN_UNSORTED = 0x4
+STATUS_ERR_BAD_INPUT = 0x100
+STATUS_ERR_TIMEOUT = 0x200
+SAMPLE_BERNOULLI = 0
+SAMPLE_PAPER_DRAW = 1
+TWO32 = 1 << 32
+
+
+class CsrStruct(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rpt", ctypes.c_void_p), ("col", ctypes.c_void_p)]
+
+
+class ConfigStruct(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("threshold", ctypes.c_uint64), ("sample_num", ctypes.c_int64),
+                ("seed", ctypes.c_uint64)]
+
+
+RESULT_BYTES = 48  # spgemm_result_t: 5 x int64 + 2 x int32
+
+_lib = None
+
+
+def library_path():
+    return str(_build.LIB)
+
+
+def load():
+    """Load the CUDA library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run paper_2207_13848_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    C = ctypes.POINTER(CsrStruct)
+    G = ctypes.POINTER(ConfigStruct)
+    sz = ctypes.c_size_t
+    lib.spgemm_workspace_size.restype = sz
+    lib.spgemm_workspace_size.argtypes = [C, C]
+    lib.spgemm_flop_per_row.argtypes = [C, C, P, P, P, sz, P]
+    lib.spgemm_predict_cr.argtypes = [C, C, G, P, P, sz, P]
+    lib.spgemm_predict_structure.argtypes = [C, C, G, P, P, P, P, P, sz, P]
+    lib.spgemm_predict_reference.argtypes = [C, C, G, P, P, P, P, P, sz, P]
+    lib.spgemm_symbolic_exact.argtypes = [C, C, P, P, P, P, sz, P]
+    lib.spgemm_sample_rows.argtypes = [ctypes.c_int64, G, P, ctypes.c_int64, P, P, sz, P]
+    lib.spgemm_validate_csr.argtypes = [C, P, P, sz, P]
+    lib.spgemm_set_profile_events.argtypes = [P, P]
+    lib.spgemm_set_profile_events.restype = ctypes.c_int
+    lib.spgemm_status_string.restype = ctypes.c_char_p
+    lib.spgemm_status_string.argtypes = [ctypes.c_int]
+    for fn in (lib.spgemm_flop_per_row, lib.spgemm_predict_cr, lib.spgemm_predict_structure,
+               lib.spgemm_predict_reference, lib.spgemm_symbolic_exact, lib.spgemm_sample_rows,
+               lib.spgemm_validate_csr):
+        fn.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(rc, what):
+    if rc != OK:
+        msg = load().spgemm_status_string(rc).decode()
+        raise RuntimeError(f"{what} failed: {msg} ({rc})")
+    return rc
+
+
+# ---- device-side operands -----------------------------------------------------
+class DeviceCSR:
+    """A CSR matrix whose int32 rpt/col arrays live in CUDA memory (torch tensors)."""
+
+    def __init__(self, rows, cols, rpt, col):
+        self.rows, self.cols = int(rows), int(cols)
+        self.rpt, self.col = rpt, col
+        self.nnz = int(col.numel())
+
+    @classmethod
+    def from_host(cls, m, device="cuda", non_blocking=False):
+        """Copy a host CSR (numpy rpt/col; e.g. workloads.CSR) to the device."""
+        torch = _torch()
+        rpt = torch.from_numpy(m.rpt).to(device, non_blocking=non_blocking)
+        col = torch.from_numpy(m.col).to(device, non_blocking=non_blocking)
+        if col.numel() == 0:
+            col = torch.zeros(1, dtype=torch.int32, device=device)[:0]
+        return cls(m.rows, m.cols, rpt, col)
+
+    def struct(self):
+        return CsrStruct(self.rows, self.cols, self.nnz, self.rpt.data_ptr(),
+                         self.col.data_ptr() if self.nnz else 0)
+
+
+def config(mode=SAMPLE_BERNOULLI, ratio=None, threshold=None, sample_num=0, seed=0):
+    """Sampling configuration; ``ratio`` in [0, 1] maps to threshold floor(ratio * 2^32)."""
+    if threshold is None:
+        threshold = 0 if ratio is None else min(TWO32, int(ratio * TWO32))
+    return ConfigStruct(int(mode), 0, int(threshold), int(sample_num), int(seed) & (2**64 - 1))
+
+
+def workspace_size(A, B=None):
+    a = A.struct()
+    b = B.struct() if B is not None else None
+    return int(load().spgemm_workspace_size(ctypes.byref(a), ctypes.byref(b) if b else None))
+
+
+class Workspace:
+    """Zero-filled device workspace, reusable across calls on one stream."""
+
+    def __init__(self, nbytes, device="cuda"):
+        torch = _torch()
+        self.nbytes = int(nbytes)
+        self.buf = torch.zeros(self.nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        self.view = self.buf[off: off + self.nbytes]
+
+    @classmethod
+    def for_operands(cls, A, B=None, device="cuda"):
+        return cls(workspace_size(A, B), device)
+
+    def ptr(self):
+        return ctypes.c_void_p(self.view.data_ptr())
+
+    def reset(self):
+        self.buf.zero_()
+
+
+def new_result(device="cuda"):
+    torch = _torch()
+    return torch.zeros(RESULT_BYTES // 8, dtype=torch.int64, device=device)
+
+
+def read_result(res):
+    """Host copy of a device result record as a dict."""
+    v = res.cpu().tolist()
+    status = v[5] & 0xFFFFFFFF
+    return dict(flop_total=v[0], flop_s=v[1], nnz_s=v[2], n_sampled=v[3], pred_total=v[4],
+                status=status)
+
+
+# ---- the C ABI, same names and argument order -----------------------------------
+def spgemm_flop_per_row(A, B, flop_row, res, ws, stream=None):
+    a, b = A.struct(), B.struct()
+    return load().spgemm_flop_per_row(ctypes.byref(a), ctypes.byref(b), _ptr(flop_row), _ptr(res),
+                                      ws.ptr(), ws.nbytes, _stream(stream))
+
+
+def spgemm_predict_cr(A, B, cfg, res, ws, stream=None):
+    a, b = A.struct(), B.struct()
+    return load().spgemm_predict_cr(ctypes.byref(a), ctypes.byref(b), ctypes.byref(cfg), _ptr(res),
+                                    ws.ptr(), ws.nbytes, _stream(stream))
+
+
+def spgemm_predict_structure(A, B, cfg, pred_row, offsets, flop_row, res, ws, stream=None):
+    a, b = A.struct(), B.struct()
+    return load().spgemm_predict_structure(ctypes.byref(a), ctypes.byref(b), ctypes.byref(cfg),
+                                           _ptr(pred_row), _ptr(offsets), _ptr(flop_row), _ptr(res),
+                                           ws.ptr(), ws.nbytes, _stream(stream))
+
+
+def spgemm_predict_reference(A, B, cfg, pred_row, offsets, flop_row, res, ws, stream=None):
+    a, b = A.struct(), B.struct()
+    return load().spgemm_predict_reference(ctypes.byref(a), ctypes.byref(b), ctypes.byref(cfg),
+                                           _ptr(pred_row), _ptr(offsets), _ptr(flop_row), _ptr(res),
+                                           ws.ptr(), ws.nbytes, _stream(stream))
+
+
+def spgemm_symbolic_exact(A, B, nnz_row, offsets, res, ws, stream=None):
+    a, b = A.struct(), B.struct()
+    return load().spgemm_symbolic_exact(ctypes.byref(a), ctypes.byref(b), _ptr(nnz_row), _ptr(offsets),
+                                        _ptr(res), ws.ptr(), ws.nbytes, _stream(stream))
+
+
+def spgemm_sample_rows(rows, cfg, ids, capacity, res, ws, stream=None):
+    return load().spgemm_sample_rows(int(rows), ctypes.byref(cfg), _ptr(ids), int(capacity), _ptr(res),
+                                     ws.ptr(), ws.nbytes, _stream(stream))
+
+
+def spgemm_validate_csr(A, res, ws, stream=None):
+    a = A.struct()
+    return load().spgemm_validate_csr(ctypes.byref(a), _ptr(res), ws.ptr(), ws.nbytes, _stream(stream))
+
+
+def spgemm_set_profile_events(before, after):
+    """Record torch.cuda.Event `before`/`after` around the main kernel of later calls
+    (None, None turns it off)."""
+    b = None if before is None else ctypes.c_void_p(before.cuda_event)
+    a = None if after is None else ctypes.c_void_p(after.cuda_event)
+    return load().spgemm_set_profile_events(b, a)
+
+
+def spgemm_status_string(code):
+    return load().spgemm_status_string(int(code)).decode()
+
+
+# ---- convenience wrappers -------------------------------------------------------
+@dataclass
+class Prediction:
+    pred: "object"             # int32[M] predicted nnz per row (or exact nnz for symbolic)
+    offsets: "object"          # int64[M+1]
+    flop: Optional["object"]   # int32[M] FLOP per row when requested
+    res: "object"              # device result record
+
+
+def _outputs(M, device, want_flop):
+    torch = _torch()
+    pred = torch.empty(max(M, 0), dtype=torch.int32, device=device)
+    offsets = torch.empty(M + 1, dtype=torch.int64, device=device)
+    flop = torch.empty(max(M, 0), dtype=torch.int32, device=device) if want_flop else None
+    return pred, offsets, flop
+
+
+def predict_structure(A, B, cfg, ws=None, want_flop=False, reference=False, stream=None):
+    """Run the proposed method (or the reference design) and return device tensors."""
+    ws = ws or Workspace.for_operands(A, B)
+    pred, offsets, flop = _outputs(A.rows, A.rpt.device, want_flop)
+    res = new_result(A.rpt.device)
+    fn = spgemm_predict_reference if reference else spgemm_predict_structure
+    _check(fn(A, B, cfg, pred, offsets, flop, res, ws, stream), fn.__name__)
+    return Prediction(pred, offsets, flop, res)
+
+
+def symbolic_exact(A, B, ws=None, stream=None):
+    ws = ws or Workspace.for_operands(A, B)
+    nnz, offsets, _ = _outputs(A.rows, A.rpt.device, False)
+    res = new_result(A.rpt.device)
+    _check(spgemm_symbolic_exact(A, B, nnz, offsets, res, ws, stream), "spgemm_symbolic_exact")
+    return Prediction(nnz, offsets, None, res)
+
+
+def flop_per_row(A, B, ws=None, stream=None):
+    torch = _torch()
+    ws = ws or Workspace.for_operands(A, B)
+    flop = torch.empty(max(A.rows, 0), dtype=torch.int32, device=A.rpt.device)
+    res = new_result(A.rpt.device)
+    _check(spgemm_flop_per_row(A, B, flop, res, ws, stream), "spgemm_flop_per_row")
+    return flop, res
+
+
+def predict_cr(A, B, cfg, ws=None, stream=None):
+    ws = ws or Workspace.for_operands(A, B)
+    res = new_result(A.rpt.device)
+    _check(spgemm_predict_cr(A, B, cfg, res, ws, stream), "spgemm_predict_cr")
+    return res
+
+
+def sample_rows(rows, cfg, capacity=None, ws=None, device="cuda", stream=None):
+    torch = _torch()
+    cap = rows if capacity is None else capacity
+    if cfg.mode == SAMPLE_PAPER_DRAW:
+        cap = max(cap, cfg.sample_num if cfg.sample_num else min(max(3 * rows // 1000, 1), 300))
+    ws = ws or Workspace(_build_ws_bytes(rows), device)
+    ids = torch.full((max(cap, 1),), -1, dtype=torch.int32, device=device)
+    res = new_result(device)
+    _check(spgemm_sample_rows(rows, cfg, ids, cap, res, ws, stream), "spgemm_sample_rows")
+    return ids, res
+
+
+def _build_ws_bytes(rows):
+    a = CsrStruct(rows, 0, 0, 0, 0)
+    return int(load().spgemm_workspace_size(ctypes.byref(a), None))
+
+
+def validate_csr(A, ws=None, stream=None):
+    ws = ws or Workspace.for_operands(A)
+    res = new_result(A.rpt.device)
+    _check(spgemm_validate_csr(A, res, ws, stream), "spgemm_validate_csr")
+    return res
+
+
+def predict_structure_host(A_host, B_host, cfg, ws=None, device="cuda", stream=None, same=False):
+    """End-to-end call on host operands: host->device copies of the CSR arrays,
+    the prediction, and device->host copies of pred/offsets and the result.
+    Returns host numpy arrays and the result dict."""
+    torch = _torch()
+    A = DeviceCSR.from_host(A_host, device, non_blocking=True)
+    B = A if same else DeviceCSR.from_host(B_host, device, non_blocking=True)
+    p = predict_structure(A, B, cfg, ws=ws, stream=stream)
+    pred = p.pred.to("cpu", non_blocking=True)
+    offsets = p.offsets.to("cpu", non_blocking=True)
+    res = p.res.to("cpu", non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return pred.numpy(), offsets.numpy(), read_result(res)

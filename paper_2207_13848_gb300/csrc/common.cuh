@@ -1,0 +1,236 @@
+// Device helpers shared by the kernels of the structure predictor: the sample
+// hash, exact integer rounding, warp/block scans, inter-block flags with
+// bounded waits, and the workspace layout.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/spgemm_predict.h"
+
+namespace spg {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Maximum number of thread blocks of one inter-block (persistent) launch; one
+// 64-byte slot per block lives in the workspace.
+constexpr int kMaxSlots = 4096;
+
+// ---------------------------------------------------------------------------
+// Workspace layout.  Everything here starts at zero (the caller zero-fills the
+// workspace once) and every successful call returns it to zero, except `epoch`,
+// which only grows: a flag counts as set when it equals the epoch of the
+// current launch, so flags never need clearing.
+// ---------------------------------------------------------------------------
+struct alignas(128) WsHeader {
+  unsigned long long f_acc;  // sum of sampled flop (f*)
+  unsigned long long z_acc;  // sum of sampled nnz (z*)
+  unsigned long long s_acc;  // number of sampled rows (|S|)
+  unsigned long long F_acc;  // total flop (F) where a kernel accumulates it
+  unsigned int heavy_count;  // rows queued for the block-per-row pass
+  unsigned int status;       // SPGEMM_STATUS_* bits (atomicOr)
+  unsigned int epoch;        // flag epoch of the previous completed launch
+  unsigned int done;         // blocks finished in the current launch
+  unsigned int pad[24];
+};
+
+struct alignas(64) Slot {
+  unsigned int carry_flag;  // = epoch when `carry` is valid
+  unsigned int total_flag;  // = epoch when `total` is valid
+  unsigned int ftot_flag;   // = epoch when `ftot` is valid
+  unsigned int pad0;
+  long long carry;  // partial FLOP of the row open at the block's end
+  long long total;  // sum of the block's per-row values (pred or nnz)
+  long long ftot;   // sum of the block's complete-row FLOP
+  long long pad1[3];
+};
+
+struct Workspace {
+  WsHeader* hdr;
+  Slot* slots;
+  int* heavy;     // [M] rows queued for the block-per-row deduplication
+  int* flop_buf;  // [M] per-row FLOP when the caller gives no flop_row buffer
+};
+
+inline size_t ws_bytes_for(int64_t M) {
+  size_t m = (size_t)(M > 0 ? M : 1);
+  size_t b = sizeof(WsHeader) + sizeof(Slot) * kMaxSlots;
+  b += ((m * 4 + 255) / 256) * 256;  // heavy
+  b += ((m * 4 + 255) / 256) * 256;  // flop_buf
+  return b;
+}
+
+inline Workspace ws_carve(void* base, int64_t M) {
+  size_t m = (size_t)(M > 0 ? M : 1);
+  char* p = static_cast<char*>(base);
+  Workspace w;
+  w.hdr = reinterpret_cast<WsHeader*>(p);
+  p += sizeof(WsHeader);
+  w.slots = reinterpret_cast<Slot*>(p);
+  p += sizeof(Slot) * kMaxSlots;
+  w.heavy = reinterpret_cast<int*>(p);
+  p += ((m * 4 + 255) / 256) * 256;
+  w.flop_buf = reinterpret_cast<int*>(p);
+  return w;
+}
+
+// ---------------------------------------------------------------------------
+// Sample hash: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014).  The state of the
+// generator started at `seed` after k steps is seed + k * gamma with gamma =
+// 0x9e3779b97f4a7c15; an output is the state passed through the finaliser
+// (xor-shift 30, multiply 0xbf58476d1ce4e5b9, xor-shift 27, multiply
+// 0x94d049bb133111eb, xor-shift 31).  h32(seed, x) takes output x + 1's high
+// half.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t sample_hash32(uint64_t seed, uint64_t x) {
+  uint64_t s = seed + (x + 1ull) * 0x9e3779b97f4a7c15ull;
+  s ^= s >> 30;
+  s *= 0xbf58476d1ce4e5b9ull;
+  s ^= s >> 27;
+  s *= 0x94d049bb133111ebull;
+  s ^= s >> 31;
+  return (uint32_t)(s >> 32);
+}
+
+// ---------------------------------------------------------------------------
+// Exact rounding of the per-row prediction without integer division: q is
+// estimated in double precision, then moved to the exact ceiling with 128-bit
+// products (the estimate is off by at most one for q < 2^32, so the loops run
+// at most a couple of times; they are bounded regardless).
+// ---------------------------------------------------------------------------
+typedef unsigned __int128 u128;
+
+// ceil(v * z / f) for 0 < v < 2^31, 0 < z <= f < 2^63 (so the result is <= v).
+__device__ __forceinline__ int pred_proposed(uint32_t v, uint64_t z, uint64_t f, double ratio) {
+  if (v == 0) return 0;
+  const u128 num = (u128)v * z;
+  uint64_t q = (uint64_t)((double)v * ratio);
+  if (q > v) q = v;
+#pragma unroll 1
+  for (int it = 0; it < 8 && (u128)q * f < num; ++it) ++q;
+#pragma unroll 1
+  for (int it = 0; it < 8 && q > 0 && (u128)(q - 1) * f >= num; ++it) --q;
+  return (int)q;
+}
+
+// ceil(v * zm / den) for the reference design: zm = z * M (< 2^94),
+// den = F * |S| (< 2^94).  Saturates at 2^31 - 1 and reports it via *sat.
+__device__ __forceinline__ int pred_reference(uint32_t v, u128 zm, u128 den, double ratio,
+                                              bool* sat) {
+  if (v == 0) return 0;
+  const double est = (double)v * ratio;
+  if (est > 2147483700.0) {
+    *sat = true;
+    return 2147483647;
+  }
+  const u128 num = (u128)v * zm;
+  uint64_t q = (uint64_t)est;
+#pragma unroll 1
+  for (int it = 0; it < 8 && (u128)q * den < num; ++it) ++q;
+#pragma unroll 1
+  for (int it = 0; it < 8 && q > 0 && (u128)(q - 1) * den >= num; ++it) --q;
+  if (q > 2147483647ull) {
+    *sat = true;
+    return 2147483647;
+  }
+  return (int)q;
+}
+
+// ---------------------------------------------------------------------------
+// Warp and block scans / reductions (int64).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T n = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive
+// prefix and writes the block total to *total.  `sm` needs NW + 1 entries.
+template <int NT>
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* sm, long long* total) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long inc = warp_incl_scan(v);
+  if (lane == 31) sm[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    long long t = lane < NW ? sm[lane] : 0;
+    long long ti = warp_incl_scan(t);
+    if (lane < NW) sm[lane] = ti - t;
+    if (lane == NW - 1) sm[NW] = ti;
+  }
+  __syncthreads();
+  long long r = sm[w] + inc - v;
+  *total = sm[NW];
+  __syncthreads();
+  return r;
+}
+
+template <int NT>
+__device__ __forceinline__ long long block_sum(long long v, long long* sm) {
+  long long t;
+  block_excl_scan<NT>(v, sm, &t);
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Inter-block flags: release/acquire at GPU scope, bounded waits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void flag_store(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned int flag_load(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits until *p == want; gives up after about one second (or 2^26 polls),
+// sets SPGEMM_STATUS_ERR_TIMEOUT and returns false.
+__device__ __noinline__ bool flag_wait(const unsigned int* p, unsigned int want,
+                                       unsigned int* status) {
+  if (flag_load(p) == want) return true;
+  const uint64_t t0 = global_ns();
+  unsigned ns = 32;
+  for (int it = 0; it < (1 << 26); ++it) {
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+    if (flag_load(p) == want) return true;
+    if ((it & 63) == 63 && global_ns() - t0 > 1000000000ull) break;
+  }
+  atomicOr(status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void set_status(WsHeader* h, unsigned bits) { atomicOr(&h->status, bits); }
+
+// Clamp a row range [b, e) read from untrusted offsets into [0, nnz].
+__device__ __forceinline__ bool clamp_range(long long& b, long long& e, long long nnz) {
+  bool ok = (b >= 0) & (e >= b) & (e <= nnz);
+  if (b < 0) b = 0;
+  if (b > nnz) b = nnz;
+  if (e > nnz) e = nnz;
+  if (e < b) e = b;
+  return ok;
+}
+
+}  // namespace spg

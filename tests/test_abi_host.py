@@ -1,0 +1,123 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads and
+exports every function include/*.h declares; host-detected errors come back as
+the documented negative codes before anything touches the device."""
+import ctypes
+import glob
+import os
+import re
+import shutil
+
+import pytest
+
+import paper_2207_13848_gb300 as sp
+from paper_2207_13848_gb300 import build as spbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(spgemm_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(spbuild.LIB) and shutil.which("nvcc") is None:
+        pytest.skip("no nvcc and no prebuilt library")
+    spbuild.build()
+    return sp.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("spgemm_flop_per_row", "spgemm_predict_cr", "spgemm_predict_structure",
+              "spgemm_predict_reference", "spgemm_symbolic_exact", "spgemm_workspace_size",
+              "spgemm_status_string", "spgemm_sample_rows", "spgemm_validate_csr"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(lib):
+    for code in (0, -1, -2, -3, -4, -5, 1, 2, 4, 0x100, 0x200, 0x101, 0x3):
+        s = sp.spgemm_status_string(code)
+        assert isinstance(s, str) and s and s != "unknown code"
+
+
+def test_struct_layouts_match_header():
+    assert ctypes.sizeof(sp.CsrStruct) == 40
+    assert ctypes.sizeof(sp.ConfigStruct) == 32
+    assert sp.RESULT_BYTES == 48
+
+
+def test_workspace_size_grows_with_rows(lib):
+    a = sp.CsrStruct(0, 5, 0, 0, 0)
+    s0 = lib.spgemm_workspace_size(ctypes.byref(a), None)
+    a = sp.CsrStruct(1 << 20, 5, 0, 0, 0)
+    s1 = lib.spgemm_workspace_size(ctypes.byref(a), None)
+    assert s0 > 0 and s1 >= s0 + 8 * (1 << 20) - 4096
+    assert lib.spgemm_workspace_size(None, None) == 0
+
+
+class _Fake:
+    """Operands with non-null fake device addresses: host checks must reject the
+    call before any pointer is used."""
+
+    def __init__(self, rows, cols, nnz):
+        self.rows, self.cols, self.nnz = rows, cols, nnz
+
+    def struct(self):
+        return sp.CsrStruct(self.rows, self.cols, self.nnz, 0x1000, 0x2000 if self.nnz else 0)
+
+
+def _call_predict(lib, A, B, cfg, ws_bytes, res=0x3000, ws=0x10000, pred=0x4000, offs=0x5000):
+    a, b = A.struct(), B.struct()
+    return lib.spgemm_predict_structure(ctypes.byref(a), ctypes.byref(b), ctypes.byref(cfg), pred, offs,
+                                        None, res, ws, ws_bytes, None)
+
+
+def test_host_errors(lib):
+    A, B = _Fake(100, 50, 300), _Fake(50, 70, 200)
+    cfg = sp.config(ratio=0.01)
+    need = sp.CsrStruct(100, 0, 0, 0, 0)
+    ws = lib.spgemm_workspace_size(ctypes.byref(need), None)
+    assert _call_predict(lib, A, _Fake(51, 70, 200), cfg, ws) == sp.ERR_DIM_MISMATCH
+    assert _call_predict(lib, A, B, cfg, ws - 1) == sp.ERR_WORKSPACE
+    assert _call_predict(lib, A, B, cfg, ws, ws=0x10010) == sp.ERR_WORKSPACE  # misaligned
+    assert _call_predict(lib, A, B, cfg, ws, res=0) == sp.ERR_INVALID_ARG
+    assert _call_predict(lib, A, B, cfg, ws, pred=0) == sp.ERR_INVALID_ARG
+    assert _call_predict(lib, _Fake(-1, 50, 0), B, cfg, ws) == sp.ERR_INVALID_ARG
+    assert _call_predict(lib, _Fake(1 << 31, 50, 0), B, cfg, 1 << 40) == sp.ERR_TOO_LARGE
+    bad = sp.config(threshold=(1 << 32) + 1)
+    assert _call_predict(lib, A, B, bad, ws) == sp.ERR_INVALID_ARG
+    bad = sp.config(mode=7, ratio=0.1)
+    assert _call_predict(lib, A, B, bad, ws) == sp.ERR_INVALID_ARG
+    bad = sp.config(mode=sp.SAMPLE_PAPER_DRAW, sample_num=101)  # more draws than rows
+    assert _call_predict(lib, A, B, bad, ws) == sp.ERR_INVALID_ARG
+    bad = sp.config(ratio=0.1)
+    bad.reserved0 = 3
+    assert _call_predict(lib, A, B, bad, ws) == sp.ERR_INVALID_ARG
+    a, b = A.struct(), B.struct()
+    assert lib.spgemm_flop_per_row(ctypes.byref(a), ctypes.byref(b), None, 0x3000, 0x10000, ws, None) \
+        == sp.ERR_INVALID_ARG
+    assert lib.spgemm_symbolic_exact(ctypes.byref(a), ctypes.byref(b), 0x4000, None, 0x3000, 0x10000, ws,
+                                     None) == sp.ERR_INVALID_ARG
+    cfgd = sp.config(mode=sp.SAMPLE_PAPER_DRAW, sample_num=10)
+    assert lib.spgemm_sample_rows(100, ctypes.byref(cfgd), 0x4000, 5, 0x3000, 0x10000, ws, None) \
+        == sp.ERR_INVALID_ARG
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(sp, "_lib", None)
+    monkeypatch.setattr(sp, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        sp.load()

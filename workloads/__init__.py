@@ -38,7 +38,12 @@ def from_coo(rows, cols, r, c, val=None, dedup=True):
     c = np.asarray(c, dtype=np.int64)
     key = r * np.int64(cols) + c
     if dedup:
-        key = np.unique(key)
+        key = np.sort(key, kind="stable")
+        if key.shape[0]:
+            keep = np.empty(key.shape[0], dtype=bool)
+            keep[0] = True
+            np.not_equal(key[1:], key[:-1], out=keep[1:])
+            key = key[keep]
         val = None if val is None else np.ones(key.shape[0], dtype=np.asarray(val).dtype)
     else:
         order = np.argsort(key, kind="stable")
