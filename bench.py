@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Throughput of the sampled-compression-ratio structure prediction on GB300.
+
+One step = one spgemm_predict_structure call: the Bernoulli row sample, the FLOP
+and exact nnz of the sampled rows, the compression ratio, the FLOP of every
+row, the per-row prediction and its exclusive scan (every step of the hot
+path), on C = A*A with A an Erdos-Renyi matrix, n = 2^20, Poisson(16) entries
+per row, uniform columns, 1 % of rows sampled.  Inputs are resident in HBM; the
+L2 is flushed (512 MiB write) before every timed step, since the operands
+(71 MB) fit in the 129 MB L2.
+
+Prints one JSON line.  Other keys: the roofline of the dominant kernel (the
+fused FLOP/prediction/scan kernel, timed with CUDA events on its stream through
+the library's profiling hook), the end-to-end number through the public API
+with host buffers, the GPU exact symbolic phase on the same input, the
+prediction errors (Sec. VI-A), the CPU oracle baseline and the SM clocks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs its own replica (weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = ("input-nnz/s and HBM GB/s of prediction vs GPU exact symbolic; "
+          "predicted-nnz rel. error")
+UNIT = "nnz/s"
+TWO32 = 1 << 32
+L2_FLUSH_BYTES = 512 << 20
+WORKLOAD = {
+    "workload": "C=A*A, A Erdos-Renyi n=2^20, Poisson(16) nnz/row, uniform columns, "
+                "int32 CSR, Bernoulli 1% row sample",
+    "n": 1 << 20, "avg_nnz_per_row": 16, "sample_ratio": 0.01, "gen_seed": 2000,
+}
+
+
+def make_input(rank=0):
+    return W.erdos_renyi(WORKLOAD["n"], WORKLOAD["avg_nnz_per_row"], WORKLOAD["gen_seed"] + rank)
+
+
+def threshold():
+    return int(WORKLOAD["sample_ratio"] * TWO32)
+
+
+# ------------------------------------------------------------------ distribution
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(backend):
+    import torch.distributed as dist
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend, rank=rank, world_size=ws)
+    return ws, rank
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def aggregate(units_local, seconds_local, device=None):
+    """Whole-job throughput of replicas: total units / slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+        s = torch.tensor([float(seconds_local)], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dist.all_reduce(s, op=dist.ReduceOp.MAX)
+        return float(u.item()), float(s.item())
+    return float(units_local), float(seconds_local)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.exe = shutil.which("nvidia-smi")
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        if not self.exe:
+            return
+        fd, self.path = tempfile.mkstemp(prefix="clocks.", suffix=".csv")
+        os.close(fd)
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen([self.exe, "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits", "-lms", "100"],
+                                     stdout=self.fh, stderr=subprocess.DEVNULL)
+        t0 = time.time()
+        while time.time() - t0 < 5 and os.path.getsize(self.path) == 0:
+            time.sleep(0.05)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ roofline inputs
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback (6.8 TB/s)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2207_13848_gb300", "csrc")
+    for name in ("common.cuh", "k_flop.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_flop_pred_predict_er_n2e20.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+source_hash:\s*([0-9a-f]+)", text)
+    if not m or m.group(2) != kernel_source_hash():
+        return None
+    return int(m.group(1))
+
+
+def algorithmic_bytes(A, f_s, n_s):
+    """Minimum bytes of one prediction (fused kernel; whole call).
+    Fused kernel: A.rpt, A.col, B.rpt (each once), pred (int32), offsets (int64).
+    Whole call adds the sampled rows' B column ids and their A offsets."""
+    M, nnz, K = A.rows, A.nnz, A.cols
+    kern = 4 * (M + 1) + 4 * nnz + 4 * (K + 1) + 4 * M + 8 * (M + 1)
+    call = kern + 4 * f_s + 8 * n_s
+    return kern, call
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def cpu_oracle_baseline(A, seconds=12.0):
+    import oracle
+    T = threshold()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.predict(A, A, oracle.BERNOULLI, n, T)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= 200:
+            break
+    return {"value": A.nnz * n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"the full workload, {n} predictions (seeds 0..{n - 1}), {dt:.1f} s"}
+
+
+def row_slice(A, r0, r1):
+    b, e = int(A.rpt[r0]), int(A.rpt[r1])
+    return W.CSR(r1 - r0, A.cols, (A.rpt[r0:r1 + 1] - b).astype(np.int32), A.col[b:e])
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on bounded samples."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    A = make_input(0)
+    T = threshold()
+    nslice = 64
+    step = A.rows // nslice
+
+    def one(k):
+        s = (k % nslice) * step
+        S = row_slice(A, s, s + step)
+        t = time.perf_counter()
+        oracle.predict(S, A, oracle.BERNOULLI, k, T)
+        return S.nnz, time.perf_counter() - t
+
+    for k in range(args.warmup):
+        one(k)
+    units, secs = 0, 0.0
+    for k in range(args.steps):
+        u, dt = one(k)
+        units += u
+        secs += dt
+    value = units / secs
+    cb = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+          "sample": f"each step: rows of one 1/{nslice} slice of A times the full A (cycling), "
+                    f"{args.steps} steps"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": dict(WORKLOAD), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+
+    import paper_2207_13848_gb300 as sp
+    from paper_2207_13848_gb300 import build as spbuild
+    from paper_2207_13848_gb300.report import estimates, row_errors
+
+    nranks, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if nranks > 1:
+        init_dist("nccl")
+    spbuild.build()
+
+    A = make_input(rank)
+    dA = sp.DeviceCSR.from_host(A, dev)
+    ws = sp.Workspace.for_operands(dA, dA, dev)
+    M = A.rows
+    pred = torch.empty(M, dtype=torch.int32, device=dev)
+    offsets = torch.empty(M + 1, dtype=torch.int64, device=dev)
+    res = sp.new_result(dev)
+    cfg = sp.config(threshold=threshold(), seed=0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def predict():
+        rc = sp.spgemm_predict_structure(dA, dA, cfg, pred, offsets, None, res, ws, stream)
+        if rc != sp.OK:
+            raise RuntimeError(sp.spgemm_status_string(rc))
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        predict()
+    torch.cuda.synchronize()
+    r0 = sp.read_result(res)
+    if r0["status"] != 0:
+        raise RuntimeError(f"device status {r0['status']}: {sp.spgemm_status_string(r0['status'])}")
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in kev:  # torch creates the CUDA event on first record; the hook needs the handle
+        a.record(stream)
+        b.record(stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.fill_(k & 0xff)
+        sp.spgemm_set_profile_events(kev[k][0], kev[k][1])
+        ev[k][0].record(stream)
+        predict()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    sp.spgemm_set_profile_events(None, None)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    t_step = sum(step_ms) / K
+    t_kern = sum(kern_ms) / K
+    units, secs = aggregate(A.nnz * K, sum(step_ms) / 1e3, dev)
+    value = units / secs
+    r = sp.read_result(res)
+
+    # ---- end to end through the public API with host buffers
+    E = max(3, min(K, args.e2e_steps))
+    h_rpt = torch.from_numpy(A.rpt).pin_memory()
+    h_col = torch.from_numpy(A.col).pin_memory()
+    h_pred = torch.empty(M, dtype=torch.int32).pin_memory()
+    h_off = torch.empty(M + 1, dtype=torch.int64).pin_memory()
+    h_res = torch.empty(res.numel(), dtype=torch.int64).pin_memory()
+    eA = sp.DeviceCSR(A.rows, A.cols, torch.empty_like(dA.rpt), torch.empty_like(dA.col))
+
+    def e2e_step():
+        eA.rpt.copy_(h_rpt, non_blocking=True)
+        eA.col.copy_(h_col, non_blocking=True)
+        rc = sp.spgemm_predict_structure(eA, eA, cfg, pred, offsets, None, res, ws, stream)
+        if rc != sp.OK:
+            raise RuntimeError(sp.spgemm_status_string(rc))
+        h_pred.copy_(pred, non_blocking=True)
+        h_off.copy_(offsets, non_blocking=True)
+        h_res.copy_(res, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        e2e_step()
+    e2e_s = time.perf_counter() - t0
+    eu, es = aggregate(A.nnz * E, e2e_s, dev)
+    h2d = 4 * (M + 1) + 4 * A.nnz
+    d2h = 4 * M + 8 * (M + 1) + sp.RESULT_BYTES
+
+    # ---- GPU exact symbolic phase on the same input
+    nnz_row = torch.empty(M, dtype=torch.int32, device=dev)
+    sres = sp.new_result(dev)
+    S = 5
+    sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(S + 1)]
+    for k in range(S + 1):
+        flush.fill_(3)
+        sev[k][0].record(stream)
+        rc = sp.spgemm_symbolic_exact(dA, dA, nnz_row, offsets, sres, ws, stream)
+        sev[k][1].record(stream)
+        if rc != sp.OK:
+            raise RuntimeError(sp.spgemm_status_string(rc))
+    torch.cuda.synchronize()
+    t_sym = sum(a.elapsed_time(b) for a, b in sev[1:]) / S
+    sr = sp.read_result(sres)
+
+    # prediction errors against the exact structure (Sec. VI-A)
+    predict()
+    torch.cuda.synchronize()
+    est = estimates(r["flop_total"], sr["pred_total"], r["flop_s"], r["nnz_s"], M, r["n_sampled"])
+    rowerr = row_errors(pred.cpu().numpy(), nnz_row.cpu().numpy())
+
+    kern_bytes, call_bytes = algorithmic_bytes(A, r["flop_s"], r["n_sampled"])
+    peak, peak_src = measured_peaks()
+    achieved = kern_bytes / (t_kern * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": nranks, "steps": K,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": dict(WORKLOAD, nnz=A.nnz, l2="flushed before every timed step (512 MiB write)",
+                       parallelism=f"replicas x{nranks}"),
+        "hbm_gbs_call": call_bytes / (t_step * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_flop_pred<predict> (FLOP per row + prediction + scan)",
+                     "algorithmic_bytes": kern_bytes, "kernel_ms": t_kern, "peak_source": peak_src,
+                     "l2_lookups_per_s": A.nnz / (t_kern * 1e-3)},
+        "e2e": {"value": eu / es, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": E},
+        "gpu_launches": 3 * K,
+        "exact_symbolic": {"ms": t_sym, "input_nnz_per_s": A.nnz / (t_sym * 1e-3),
+                           "prediction_speedup": t_sym / t_step, "Z": sr["pred_total"]},
+        "accuracy": {"eps1": est["eps1"], "eps_f": est["eps_f"], "eps2": est["eps2"],
+                     "row_rel_err_mean": rowerr["mean"], "row_rel_err_max": rowerr["max"],
+                     "F": r["flop_total"], "f_s": r["flop_s"], "z_s": r["nnz_s"],
+                     "n_sampled": r["n_sampled"]},
+        "clocks": clk,
+    }
+    if nranks == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_baseline(A, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
