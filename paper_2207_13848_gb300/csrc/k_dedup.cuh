@@ -18,7 +18,8 @@ namespace spg {
 // ---------------------------------------------------------------- parameters
 constexpr int kDedupThreads = 256;            // threads per block of the warp-per-row pass
 constexpr int kDedupWarps = kDedupThreads / 32;
-constexpr int kWarpTable = 2048;              // hash slots per warp
+constexpr int kWarpTable = 1024;              // hash slots per warp
+constexpr int kListCap = 2048;                // sampled rows staged per block before processing
 constexpr int kWarpCap = kWarpTable / 2;      // products per row for the warp path
 constexpr int kHeavyThreads = 1024;           // threads per block of the heavy pass
 constexpr int kBlockHashCap = 16384;          // products per row for the block hash path
@@ -134,8 +135,12 @@ __device__ long long dedup_row_warp(const DedupArgs& a, int row, int* tbl, long 
     __syncwarp();
     int cnt = 0;
     for (long long g = rb; g < re; g += 32) {
-      long long s = 0, len = 0;
-      if (g + lane < re) b_row(a, __ldg(a.a_col + g + lane), s, len, bad);
+      long long s = s0, len = len0;  // the first group was read by the FLOP loop
+      if (g != rb) {
+        s = 0;
+        len = 0;
+        if (g + lane < re) b_row(a, __ldg(a.a_col + g + lane), s, len, bad);
+      }
       const int ilen = (int)len;
       const int inc = warp_incl_scan(ilen);
       const int excl = inc - ilen;
@@ -174,42 +179,49 @@ __device__ long long dedup_row_warp(const DedupArgs& a, int row, int* tbl, long 
 }
 
 // Pass 1: candidates -> rows (sample or all rows), warp-per-row deduplication.
-// Each block takes a contiguous slice of the candidates, compacts the selected
-// rows of a batch into shared memory and hands them to its warps.
+// Each block takes a contiguous slice of the candidates, hashes them and stages
+// the selected rows in shared memory (up to kListCap at a time), then hands the
+// staged rows to its warps, so the warps' per-row memory latencies overlap.
 __global__ void __launch_bounds__(kDedupThreads) k_dedup_rows(DedupArgs a) {
   extern __shared__ int dyn[];
   int* tbl = dyn + (threadIdx.x >> 5) * kWarpTable;
-  __shared__ int list[kDedupThreads];
+  __shared__ int list[kListCap];
   __shared__ int list_n;
   __shared__ long long red[kDedupWarps + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long c_beg = (long long)blockIdx.x * a.n_cand / gridDim.x;
   const long long c_end = (long long)(blockIdx.x + 1) * a.n_cand / gridDim.x;
   long long f_loc = 0, z_loc = 0, s_loc = 0;
-  for (long long base = c_beg; base < c_end; base += kDedupThreads) {
+  long long base = c_beg;
+  while (base < c_end) {
     if (threadIdx.x == 0) list_n = 0;
     __syncthreads();
-    const long long cand = base + threadIdx.x;
-    bool take = false;
-    int row = 0;
-    if (cand < c_end) {
-      if (a.src == kSrcAllRows) {
-        take = true;
-        row = (int)cand;
-      } else if (a.src == kSrcBernoulli) {
-        take = (uint64_t)sample_hash32(a.seed, (uint64_t)cand) < a.threshold;
-        row = (int)cand;
-      } else {
-        take = true;
-        row = (int)(((uint64_t)sample_hash32(a.seed, (uint64_t)cand) * (uint64_t)a.M) >> 32);
+    // stage selected rows until the list could overflow or the slice ends
+    for (;;) {
+      const long long cand = base + threadIdx.x;
+      bool take = false;
+      int row = 0;
+      if (cand < c_end) {
+        if (a.src == kSrcAllRows) {
+          take = true;
+          row = (int)cand;
+        } else if (a.src == kSrcBernoulli) {
+          take = (uint64_t)sample_hash32(a.seed, (uint64_t)cand) < a.threshold;
+          row = (int)cand;
+        } else {
+          take = true;
+          row = (int)(((uint64_t)sample_hash32(a.seed, (uint64_t)cand) * (uint64_t)a.M) >> 32);
+        }
       }
+      const unsigned bal = __ballot_sync(kFull, take);
+      int wbase = 0;
+      if (lane == 0 && bal) wbase = atomicAdd(&list_n, __popc(bal));
+      wbase = __shfl_sync(kFull, wbase, 0);
+      if (take) list[wbase + __popc(bal & ((1u << lane) - 1u))] = row;
+      base += kDedupThreads;
+      __syncthreads();
+      if (base >= c_end || list_n > kListCap - kDedupThreads) break;
     }
-    const unsigned bal = __ballot_sync(kFull, take);
-    int wbase = 0;
-    if (lane == 0 && bal) wbase = atomicAdd(&list_n, __popc(bal));
-    wbase = __shfl_sync(kFull, wbase, 0);
-    if (take) list[wbase + __popc(bal & ((1u << lane) - 1u))] = row;
-    __syncthreads();
     const int n = list_n;
     for (int e = warp; e < n; e += kDedupWarps) {
       const int r = list[e];
