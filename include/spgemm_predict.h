@@ -49,6 +49,8 @@ extern "C" {
 #define SPGEMM_ERR_WORKSPACE (-3)    /* ws_bytes < spgemm_workspace_size(A, B) */
 #define SPGEMM_ERR_CUDA (-4)         /* a CUDA launch or query failed */
 #define SPGEMM_ERR_TOO_LARGE (-5)    /* a size does not fit the int32 index range */
+#define SPGEMM_ERR_STATIC_CAPACITY (-6) /* spgemm_predict_structure_static: A.rows exceeds
+                                           SPGEMM_STATIC_MAX_ROWS */
 
 /* ---- device status bits (res->status) ------------------------------------------ */
 #define SPGEMM_STATUS_OK 0
@@ -179,6 +181,33 @@ int spgemm_validate_csr(const spgemm_csr_t* A, spgemm_result_t* res, void* ws, s
  * NULL, NULL turns the hook off.  The setting is process-wide; it is meant for
  * benchmarks, not for concurrent use from several threads.  Returns SPGEMM_OK. */
 int spgemm_set_profile_events(void* before, void* after);
+
+/* spgemm_predict_structure without a caller-supplied workspace.  The paper has
+ * no counterpart: this is a library utility for callers that cannot allocate
+ * device memory themselves, for example a host program whose device memory is
+ * owned by another allocator it cannot reach (a framework's caching allocator
+ * hands it only finished tensors), or a latency-critical loop that must not call
+ * cudaMalloc because that call can synchronise the whole device.
+ *
+ * The scratch space is a fixed array of device memory compiled into the library,
+ * sized for A.rows <= SPGEMM_STATIC_MAX_ROWS (about 17 MB).  Every GPU that loads
+ * the library holds it until the process exits.  Larger problems are rejected
+ * with SPGEMM_ERR_STATIC_CAPACITY before anything is queued.  The call allocates
+ * nothing (no cudaMalloc/cudaFree, no allocating library routine): the caller
+ * still passes the inputs, outputs and result record, as for
+ * spgemm_predict_structure, and gets the same results.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and clears its bookkeeping part
+ * (262 KB, a cudaMemsetAsync on `stream`) before use, so calls that overlap on
+ * the GPU (on different streams, or from several threads) race and must not be
+ * issued. */
+#define SPGEMM_STATIC_MAX_ROWS (1ll << 21)
+int spgemm_predict_structure_static(const spgemm_csr_t* A, const spgemm_csr_t* B,
+                                    const spgemm_config_t* cfg, int32_t* pred_row,
+                                    int64_t* offsets, int32_t* flop_row, spgemm_result_t* res,
+                                    void* stream);
 
 /* Static description of a host return code or of a status bit set. */
 const char* spgemm_status_string(int code);

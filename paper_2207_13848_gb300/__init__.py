@@ -26,6 +26,8 @@ ERR_DIM_MISMATCH = -2
 ERR_WORKSPACE = -3
 ERR_CUDA = -4
 ERR_TOO_LARGE = -5
+ERR_STATIC_CAPACITY = -6
+STATIC_MAX_ROWS = 1 << 21
 STATUS_WARN_EMPTY_SAMPLE = 0x1
 STATUS_WARN_SATURATED = 0x2
 STATUS_WARN_UNSORTED = 0x4
@@ -79,6 +81,8 @@ def load():
     lib.spgemm_symbolic_exact.argtypes = [C, C, P, P, P, P, sz, P]
     lib.spgemm_sample_rows.argtypes = [ctypes.c_int64, G, P, ctypes.c_int64, P, P, sz, P]
     lib.spgemm_validate_csr.argtypes = [C, P, P, sz, P]
+    lib.spgemm_predict_structure_static.argtypes = [C, C, G, P, P, P, P, P]
+    lib.spgemm_predict_structure_static.restype = ctypes.c_int
     lib.spgemm_set_profile_events.argtypes = [P, P]
     lib.spgemm_set_profile_events.restype = ctypes.c_int
     lib.spgemm_status_string.restype = ctypes.c_char_p
@@ -209,6 +213,17 @@ def spgemm_predict_reference(A, B, cfg, pred_row, offsets, flop_row, res, ws, st
     return load().spgemm_predict_reference(ctypes.byref(a), ctypes.byref(b), ctypes.byref(cfg),
                                            _ptr(pred_row), _ptr(offsets), _ptr(flop_row), _ptr(res),
                                            ws.ptr(), ws.nbytes, _stream(stream))
+
+
+def spgemm_predict_structure_static(A, B, cfg, pred_row, offsets, flop_row, res, stream=None):
+    """spgemm_predict_structure with the library's own fixed scratch array instead
+    of a workspace, for callers that cannot allocate device memory (no
+    allocation happens inside; the first call per device must precede any
+    stream capture, and overlapping calls race)."""
+    a, b = A.struct(), B.struct()
+    return load().spgemm_predict_structure_static(ctypes.byref(a), ctypes.byref(b), ctypes.byref(cfg),
+                                                  _ptr(pred_row), _ptr(offsets), _ptr(flop_row),
+                                                  _ptr(res), _stream(stream))
 
 
 def spgemm_symbolic_exact(A, B, nnz_row, offsets, res, ws, stream=None):

@@ -216,6 +216,26 @@ int predict_common(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_co
   return reference ? launch_flop<kModeReference>(L, f, st) : launch_flop<kModePredict>(L, f, st);
 }
 
+// ---- scratch for spgemm_predict_structure_static --------------------------------
+// The workspace of a problem with SPGEMM_STATIC_MAX_ROWS rows, as one file-scope
+// device array.  In host code the name is only a stand-in for the device
+// object: its device address comes from cudaGetSymbolAddress, looked up once per
+// device below and passed to the kernels.
+constexpr size_t kStaticHeaderBytes = sizeof(WsHeader) + sizeof(Slot) * kMaxSlots;
+constexpr size_t kStaticRowBytes = ((size_t)SPGEMM_STATIC_MAX_ROWS * 4 + 255) / 256 * 256;
+constexpr size_t kStaticBytes = kStaticHeaderBytes + 2 * kStaticRowBytes;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+void* g_static_ptr[kMaxDevices];
+cudaError_t g_static_err[kMaxDevices];
+std::once_flag g_static_once[kMaxDevices];
+
+void init_static_scratch(int dev) {
+  void* p = nullptr;
+  g_static_err[dev] = cudaGetSymbolAddress(&p, g_static_scratch);
+  g_static_ptr[dev] = g_static_err[dev] == cudaSuccess ? p : nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -318,6 +338,24 @@ int spgemm_validate_csr(const spgemm_csr_t* A, spgemm_result_t* res, void* ws, s
   return cudaGetLastError() == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 
+int spgemm_predict_structure_static(const spgemm_csr_t* A, const spgemm_csr_t* B,
+                                    const spgemm_config_t* cfg, int32_t* pred_row,
+                                    int64_t* offsets, int32_t* flop_row, spgemm_result_t* res,
+                                    void* stream) {
+  if (!csr_ok(A)) return SPGEMM_ERR_INVALID_ARG;
+  if (A->rows > SPGEMM_STATIC_MAX_ROWS) return SPGEMM_ERR_STATIC_CAPACITY;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SPGEMM_ERR_CUDA;
+  std::call_once(g_static_once[dev], init_static_scratch, dev);
+  void* ws = g_static_ptr[dev];
+  if (!ws) return SPGEMM_ERR_CUDA;
+  if (ws_bytes_for(A->rows) > kStaticBytes) return SPGEMM_ERR_STATIC_CAPACITY;
+  // Header, per-block slots and flag epoch start from zero on every call.
+  if (cudaMemsetAsync(ws, 0, kStaticHeaderBytes, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return SPGEMM_ERR_CUDA;
+  return predict_common(A, B, cfg, pred_row, offsets, flop_row, res, ws, kStaticBytes, stream, false);
+}
+
 int spgemm_set_profile_events(void* before, void* after) {
   g_prof_before.store(static_cast<cudaEvent_t>(before));
   g_prof_after.store(static_cast<cudaEvent_t>(after));
@@ -332,6 +370,8 @@ const char* spgemm_status_string(int code) {
     case SPGEMM_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
     case SPGEMM_ERR_CUDA: return "CUDA launch or query failed";
     case SPGEMM_ERR_TOO_LARGE: return "size exceeds the int32 index range";
+    case SPGEMM_ERR_STATIC_CAPACITY:
+      return "A.rows exceeds the static scratch of spgemm_predict_structure_static (SPGEMM_STATIC_MAX_ROWS)";
     case SPGEMM_STATUS_WARN_EMPTY_SAMPLE: return "warning: empty sample, prediction fell back to FLOP";
     case SPGEMM_STATUS_WARN_SATURATED: return "warning: a prediction saturated at 2^31-1";
     case SPGEMM_STATUS_WARN_UNSORTED: return "warning: a row is not strictly increasing";
