@@ -314,6 +314,11 @@ def run_ours(args):
     units, secs = aggregate(A.nnz * K, sum(step_ms) / 1e3, dev)
     value = units / secs
     r = sp.read_result(res)
+    if r["status"] & (sp.STATUS_ERR_BAD_INPUT | sp.STATUS_ERR_TIMEOUT):
+        raise RuntimeError(f"device status {r['status']} after the timed steps")
+    step_sorted = sorted(step_ms)
+    step_dist = {"min": step_sorted[0], "p50": step_sorted[K // 2], "p99": step_sorted[min(K - 1, (99 * K) // 100)],
+                 "max": step_sorted[-1]}
 
     # ---- end to end through the public API with host buffers
     E = max(3, min(K, args.e2e_steps))
@@ -374,7 +379,8 @@ def run_ours(args):
     traffic = profiled_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": nranks, "steps": K,
-        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": t_step, "step_ms": step_dist, "higher_is_better": True,
+        "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": dict(WORKLOAD, nnz=A.nnz, l2="flushed before every timed step (512 MiB write)",
                        parallelism=f"replicas x{nranks}"),

@@ -158,8 +158,10 @@ int launch_dedup(const DeviceLimits* L, const DedupArgs& d, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 
+// flop_row may be null in predict mode (the per-row FLOP is then not stored);
+// the other modes keep it in the workspace when the caller gives no buffer.
 FlopArgs flop_args(const spgemm_csr_t* A, const spgemm_csr_t* B, const Workspace& w, int* flop,
-                   int* pred, int64_t* offsets, spgemm_result_t* res) {
+                   int* pred, int64_t* offsets, spgemm_result_t* res, bool flop_optional) {
   FlopArgs f;
   f.M = A->rows;
   f.K = A->cols;
@@ -168,7 +170,8 @@ FlopArgs flop_args(const spgemm_csr_t* A, const spgemm_csr_t* B, const Workspace
   f.a_rpt = A->rpt;
   f.a_col = A->col;
   f.b_rpt = B->rpt;
-  f.flop = flop ? flop : w.flop_buf;
+  f.flop = flop ? flop : (flop_optional ? nullptr : w.flop_buf);
+  f.vec_ok = ((reinterpret_cast<uintptr_t>(A->col) | reinterpret_cast<uintptr_t>(B->rpt)) & 15) == 0;
   f.pred = pred;
   f.offsets = reinterpret_cast<long long*>(offsets);
   f.ws = w;
@@ -212,7 +215,7 @@ int predict_common(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_co
   d.threshold = cfg->threshold;
   d.n_cand = n_cand;
   if ((rc = launch_dedup(L, d, st))) return rc;
-  FlopArgs f = flop_args(A, B, w, flop_row, pred_row, offsets, res);
+  FlopArgs f = flop_args(A, B, w, flop_row, pred_row, offsets, res, !reference);
   return reference ? launch_flop<kModeReference>(L, f, st) : launch_flop<kModePredict>(L, f, st);
 }
 
@@ -254,7 +257,7 @@ int spgemm_flop_per_row(const spgemm_csr_t* A, const spgemm_csr_t* B, int32_t* f
   const DeviceLimits* L = limits();
   if (!L) return SPGEMM_ERR_CUDA;
   Workspace w = ws_carve(ws, A->rows);
-  FlopArgs f = flop_args(A, B, w, flop_row, nullptr, nullptr, res);
+  FlopArgs f = flop_args(A, B, w, flop_row, nullptr, nullptr, res, false);
   return launch_flop<kModeFlop>(L, f, static_cast<cudaStream_t>(stream));
 }
 

@@ -10,18 +10,21 @@
 // is one whose end marker lies in c's range; the part of a row that started in
 // an earlier block arrives as a carry published by that block.
 //
-// Inside a block the rows are taken in windows of kWin rows (their end offsets
-// staged in shared memory); the window's nonzeros are processed kChunk at a
-// time, kItems consecutive nonzeros per thread.  A thread finds the row of its
-// first nonzero by binary search in the staged ends, gathers the B row lengths
-// of its nonzeros (the gathers are issued before they are consumed), and adds
-// per-row partial sums into shared memory.
+// Inside a block, A's nonzeros are taken kChunk at a time (the chunk grid is
+// aligned to 16 bytes, so every thread reads its kItems consecutive column ids
+// with two 128-bit loads, issued one chunk ahead).  Each nonzero's B row length
+// comes from one 128-bit load around B.rpt[c] (a second load only when the pair
+// straddles it); the lengths go to shared memory.  Then one thread per row sums
+// its row's segment of the chunk (segments longer than kLong are summed by
+// whole warps), into per-row sums of the current window of kWin rows, whose end
+// offsets sit in shared memory.  When a window's rows are complete it is
+// emitted: the prediction of each row is computed once and written.
 //
-// All blocks are co-resident (cooperative launch).  Blocks exchange three
-// things through flags in the workspace, each wait bounded: the carry of a row
-// that spans blocks, the block's total of predicted nnz (for the scan), and, in
-// the reference design, the block's FLOP total (F is needed before any
-// prediction).
+// All blocks are co-resident (the grid never exceeds what the device holds at
+// once).  Blocks exchange three things through flags in the workspace, each
+// wait bounded: the carry of a row that spans blocks, the block's total of
+// predicted nnz (for the scan), and, in the reference design, the block's FLOP
+// total (F is needed before any prediction).
 #pragma once
 
 #include "common.cuh"
@@ -32,7 +35,9 @@ constexpr int kFlopThreads = 512;
 constexpr int kItems = 8;                       // nonzeros per thread per chunk
 constexpr int kChunk = kFlopThreads * kItems;   // nonzeros per chunk
 constexpr int kWin = 2048;                      // rows per window
-constexpr int kRowsPerThread = 4;               // rows per thread in the write-out
+constexpr int kLong = 64;                       // longer row segments are summed by warps
+constexpr int kMaxLong = kChunk / kLong + 1;
+constexpr int kRowsPerThread = 4;               // rows per thread in the offsets pass
 
 enum FlopMode { kModeFlop = 0, kModePredict = 1, kModeReference = 2 };
 
@@ -41,9 +46,10 @@ struct FlopArgs {
   const int* a_rpt;
   const int* a_col;
   const int* b_rpt;
-  int* flop;             // [M] per-row FLOP (caller's flop_row or workspace)
+  int* flop;             // [M] per-row FLOP: caller's flop_row, or null (predict) / workspace (others)
   int* pred;             // [M] per-row prediction (predict / reference)
   long long* offsets;    // [M + 1]
+  int vec_ok;            // A.col and B.rpt are 16-byte aligned: 128-bit loads allowed
   Workspace ws;
   spgemm_result_t* res;
 };
@@ -69,29 +75,41 @@ __device__ long long merge_path_rows(const int* rpt, long long M, long long d) {
 }
 
 struct FlopShared {
-  int ends[kWin];
-  int fsum[kWin];
+  alignas(16) int lbuf[kChunk];  // B row lengths of the chunk's nonzeros
+  int ends[kWin];    // end offset of each window row (clamped to the block's range)
+  int fsum[kWin];    // per-row FLOP of the window rows
+  int long_k[kMaxLong], long_a[kMaxLong], long_b[kMaxLong];
+  int long_n;
+  int win_js;        // first nonzero of the window's first row (clamped)
   long long red[kFlopThreads / 32 + 1];
   long long bc[8];
 };
 
-__device__ __forceinline__ int upper_bound_smem(const int* v, int n, int key) {
-  int lo = 0, hi = n;
+// First index k in [lo, n) with v[k] >= key, or n.
+__device__ __forceinline__ int lower_bound_smem(const int* v, int lo, int n, int key) {
+  int hi = n;
   while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (v[mid] <= key) lo = mid + 1; else hi = mid;
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] < key) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
 
+// B row length of column id c, with bounds checks; one 128-bit load when possible.
+struct LenLoad {
+  int4 v;
+  int extra;
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(kFlopThreads) k_flop_pred(FlopArgs a) {
+__global__ void __launch_bounds__(kFlopThreads, 2) k_flop_pred(FlopArgs a) {
   __shared__ FlopShared sm;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int G = gridDim.x, c = blockIdx.x;
   WsHeader* hdr = a.ws.hdr;
   const unsigned ep = *reinterpret_cast<volatile unsigned*>(&hdr->epoch) + 1u;
   Slot* slots = a.ws.slots;
+  const int K = (int)a.K;
 
   // ---- this block's share of the merged sequence
   const long long D = a.M + a.nnzA;
@@ -106,91 +124,190 @@ __global__ void __launch_bounds__(kFlopThreads) k_flop_pred(FlopArgs a) {
       sm.bc[3] = min(max(d1 - i1, 0ll), (long long)a.nnzA);
     }
   }
+  if (t == 0) sm.long_n = 0;
   __syncthreads();
-  const long long i0 = sm.bc[0], j0 = sm.bc[1], i1 = sm.bc[2];
-  const long long j1 = max(sm.bc[3], j0);
-  const bool tail_row = i1 < a.M;              // row i1 continues into the next block
-  const long long r_end = tail_row ? i1 + 1 : i1;
-  const bool head_split = (i0 < a.M) && (c > 0) && ((long long)__ldg(a.a_rpt + i0) < j0);
+  const int i0 = (int)sm.bc[0], j0 = (int)sm.bc[1], i1 = (int)sm.bc[2];
+  const int j1 = (int)max(sm.bc[3], sm.bc[1]);
+  const bool tail_row = i1 < a.M;  // row i1 continues into the next block
+  const int r_end = tail_row ? i1 + 1 : i1;
+  const bool head_split = (i0 < a.M) && (c > 0) && (__ldg(a.a_rpt + i0) < j0);
 
   bool bad = false;
-  const double ratio = (MODE == kModePredict && hdr->f_acc) ? (double)hdr->z_acc / (double)hdr->f_acc : 0.0;
+  const unsigned long long fz = hdr->f_acc, zz = hdr->z_acc;
+  const double ratio = (MODE == kModePredict && fz) ? (double)zz / (double)fz : 0.0;
   long long ftot = 0, ptot = 0;  // per-thread sums over complete rows
   long long head_part = 0, tail_part = 0;
 
-  // ---- phase 1: FLOP of every row touching this block's items
-  for (long long wa = i0; wa < r_end; wa += kWin) {
-    const int nw = (int)min((long long)kWin, r_end - wa);
+  // ---- window of rows [wa, wa + nw)
+  int wa = i0, nw = 0;
+  auto load_window = [&](int start) {
+    wa = start;
+    nw = min(kWin, r_end - wa);
     for (int k = t; k < nw; k += kFlopThreads) {
-      const long long r = wa + k;
-      long long e = (r == i1) ? j1 : (long long)__ldg(a.a_rpt + r + 1);
+      const int r = wa + k;
+      int e = (tail_row && r == i1) ? j1 : __ldg(a.a_rpt + r + 1);
       e = min(max(e, j0), j1);
-      sm.ends[k] = (int)e;
+      sm.ends[k] = e;
       sm.fsum[k] = 0;
     }
-    long long js = max((long long)__ldg(a.a_rpt + wa), j0);
-    js = min(js, j1);
-    __syncthreads();
-    const long long je = max((long long)sm.ends[nw - 1], js);
-    for (long long s = js; s < je; s += kChunk) {
-      const long long jt = s + (long long)t * kItems;
-      if (jt < je) {
-        const int n_u = (int)min((long long)kItems, je - jt);
-        int col[kItems];
-#pragma unroll
-        for (int u = 0; u < kItems; ++u) col[u] = u < n_u ? __ldg(a.a_col + jt + u) : 0;
-        int lo_[kItems], hi_[kItems];
-#pragma unroll
-        for (int u = 0; u < kItems; ++u) {
-          lo_[u] = 0;
-          hi_[u] = 0;
-          if (u < n_u) {
-            if ((unsigned)col[u] < (unsigned long long)a.K) {
-              lo_[u] = __ldg(a.b_rpt + col[u]);
-              hi_[u] = __ldg(a.b_rpt + col[u] + 1);
-            } else {
-              bad = true;
-            }
-          }
-        }
-        int k = upper_bound_smem(sm.ends, nw, (int)jt);
-        int acc = 0;
-#pragma unroll
-        for (int u = 0; u < kItems; ++u) {
-          if (u < n_u) {
-            const int j = (int)(jt + u);
-            while (k < nw - 1 && j >= sm.ends[k]) {
-              if (acc) atomicAdd(&sm.fsum[k], acc);
-              acc = 0;
-              ++k;
-            }
-            int len = hi_[u] - lo_[u];
-            if (len < 0 || lo_[u] < 0 || (long long)hi_[u] > a.nnzB) {
-              bad = true;
-              len = 0;
-            }
-            acc += len;
-          }
-        }
-        if (acc) atomicAdd(&sm.fsum[min(k, nw - 1)], acc);
-      }
-    }
-    __syncthreads();
+    if (t == 0) sm.win_js = min(max(__ldg(a.a_rpt + wa), j0), j1);
+  };
+  auto emit_window = [&]() {
     for (int k = t; k < nw; k += kFlopThreads) {
-      const long long r = wa + k;
+      const int r = wa + k;
       const int v = sm.fsum[k];
       if (tail_row && r == i1) {
-        tail_part = v;  // only one thread sees it
+        tail_part = v;  // seen by one thread only
       } else if (head_split && r == i0) {
         head_part = v;
       } else {
-        a.flop[r] = v;
         ftot += v;
         if (MODE == kModePredict) {
-          ptot += (hdr->f_acc == 0) ? v : pred_proposed((uint32_t)v, hdr->z_acc, hdr->f_acc, ratio);
+          const int p = fz == 0 ? v : pred_proposed((uint32_t)v, zz, fz, ratio);
+          a.pred[r] = p;
+          ptot += p;
+          if (a.flop) a.flop[r] = v;
+        } else {
+          a.flop[r] = v;
         }
       }
     }
+  };
+
+  // ---- column ids of this thread's items of a chunk, as two 128-bit loads
+  auto load_cols = [&](int cs, int* col) {
+    const int q0 = cs + t * kItems;
+    if (a.vec_ok && (long long)q0 + kItems <= a.nnzA && q0 >= 0) {
+      const int4 x = __ldg(reinterpret_cast<const int4*>(a.a_col + q0));
+      const int4 y = __ldg(reinterpret_cast<const int4*>(a.a_col + q0 + 4));
+      col[0] = x.x; col[1] = x.y; col[2] = x.z; col[3] = x.w;
+      col[4] = y.x; col[5] = y.y; col[6] = y.z; col[7] = y.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < kItems; ++u) {
+        const int q = q0 + u;
+        col[u] = (q >= 0 && q < a.nnzA) ? __ldg(a.a_col + q) : 0;
+      }
+    }
+  };
+
+  load_window(i0);
+  const int cs0 = j0 & ~3;
+  int col[kItems];
+  if (cs0 < j1) load_cols(cs0, col);
+  int ka = 0;
+  __syncthreads();
+
+  // ---- phase 1: FLOP of every row touching this block's items
+  for (int cs = cs0; cs < j1; cs += kChunk) {
+    const int lo = max(cs, j0), hi = min(cs + kChunk, j1);
+    // B row lengths of this thread's items, gathers issued four at a time
+    int len[kItems];
+#pragma unroll
+    for (int h = 0; h < kItems; h += 4) {
+      LenLoad ld[4];
+      bool use[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = cs + t * kItems + h + u;
+        const int cc = col[h + u];
+        use[u] = q >= lo && q < hi;
+        ld[u].v = make_int4(0, 0, 0, 0);
+        ld[u].extra = 0;
+        if (use[u]) {
+          if ((unsigned)cc >= (unsigned)K) {
+            bad = true;
+            use[u] = false;
+          } else if (a.vec_ok && (cc | 3) <= K) {
+            ld[u].v = __ldg(reinterpret_cast<const int4*>(a.b_rpt) + (cc >> 2));
+            if ((cc & 3) == 3) ld[u].extra = __ldg(a.b_rpt + cc + 1);
+          } else {
+            ld[u].v.x = __ldg(a.b_rpt + cc);
+            ld[u].v.y = __ldg(a.b_rpt + cc + 1);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int cc = col[h + u];
+        int b0, b1;
+        if (a.vec_ok && (cc | 3) <= K) {
+          const int r = cc & 3;
+          b0 = r == 0 ? ld[u].v.x : r == 1 ? ld[u].v.y : r == 2 ? ld[u].v.z : ld[u].v.w;
+          b1 = r == 0 ? ld[u].v.y : r == 1 ? ld[u].v.z : r == 2 ? ld[u].v.w : ld[u].extra;
+        } else {
+          b0 = ld[u].v.x;
+          b1 = ld[u].v.y;
+        }
+        int l = b1 - b0;
+        if (use[u] && (l < 0 || b0 < 0 || (long long)b1 > a.nnzB)) {
+          bad = true;
+          l = 0;
+        }
+        len[h + u] = use[u] ? l : 0;
+      }
+    }
+    {
+      // prefetch the next chunk's column ids
+      if (cs + kChunk < j1) load_cols(cs + kChunk, col);
+      int4* lb = reinterpret_cast<int4*>(sm.lbuf + t * kItems);
+      lb[0] = make_int4(len[0], len[1], len[2], len[3]);
+      lb[1] = make_int4(len[4], len[5], len[6], len[7]);
+    }
+    __syncthreads();
+    // one thread per row of the window overlapping [pos, hi)
+    int pos = lo;
+    for (;;) {
+      const int kb = lower_bound_smem(sm.ends, ka, nw, hi);  // first row ending at or after hi
+      const int kend = min(kb, nw - 1);
+      for (int k = ka + t; k <= kend; k += kFlopThreads) {
+        const int rs = k == 0 ? sm.win_js : sm.ends[k - 1];
+        const int sa = max(rs, pos), sb = min(sm.ends[k], hi);
+        if (sb - sa > kLong) {
+          const int e = atomicAdd(&sm.long_n, 1);
+          sm.long_k[e] = k;
+          sm.long_a[e] = sa;
+          sm.long_b[e] = sb;
+        } else {
+          int acc = 0;
+          for (int q = sa; q < sb; ++q) acc += sm.lbuf[q - cs];
+          sm.fsum[k] += acc;
+        }
+      }
+      __syncthreads();
+      const int nl = sm.long_n;
+      if (nl) {
+        for (int e = 0; e < nl; ++e) {
+          const int sa = sm.long_a[e], sb = sm.long_b[e];
+          int acc = 0;
+          for (int q = sa + t; q < sb; q += kFlopThreads) acc += sm.lbuf[q - cs];
+          acc = warp_sum(acc);
+          if (lane == 0 && acc) atomicAdd(&sm.fsum[sm.long_k[e]], acc);
+        }
+        __syncthreads();
+        if (t == 0) sm.long_n = 0;
+      }
+      if (kb < nw) {
+        ka = kend;
+        break;
+      }
+      // every row of the window ends before hi: emit it, move to the next rows
+      emit_window();
+      __syncthreads();
+      load_window(wa + nw);
+      __syncthreads();
+      pos = sm.win_js;
+      ka = 0;
+      if (nw <= 0) break;
+    }
+  }
+  // rows left after the last nonzero (the last window and trailing empty rows)
+  if (nw > 0) emit_window();
+  __syncthreads();
+  while (wa + nw < r_end) {
+    load_window(wa + nw);
+    __syncthreads();
+    emit_window();
     __syncthreads();
   }
 
@@ -215,10 +332,15 @@ __global__ void __launch_bounds__(kFlopThreads) k_flop_pred(FlopArgs a) {
         long long cin = 0;
         if (flag_wait(&slots[c - 1].carry_flag, ep, &hdr->status)) cin = slots[c - 1].carry;
         const long long v0 = cin + head_sum;
-        a.flop[i0] = (int)v0;
         extra_f = v0;
-        if (MODE == kModePredict)
-          extra_p = (hdr->f_acc == 0) ? v0 : pred_proposed((uint32_t)v0, hdr->z_acc, hdr->f_acc, ratio);
+        if (MODE == kModePredict) {
+          const int p = fz == 0 ? (int)v0 : pred_proposed((uint32_t)v0, zz, fz, ratio);
+          a.pred[i0] = p;
+          if (a.flop) a.flop[i0] = (int)v0;
+          extra_p = p;
+        } else {
+          a.flop[i0] = (int)v0;
+        }
       }
     }
     sm.bc[4] = extra_f;
@@ -230,10 +352,7 @@ __global__ void __launch_bounds__(kFlopThreads) k_flop_pred(FlopArgs a) {
 
   if (MODE != kModeFlop) {
     // ---- the reference design needs F before any prediction
-    double ratio_ref = 0.0;
-    u128 zm = 0, den = 0;
     bool sat = false;
-    const bool ref_empty = hdr->s_acc == 0;
     if (MODE == kModeReference) {
       if (t == 0) {
         slots[c].ftot = blk_f;
@@ -248,13 +367,16 @@ __global__ void __launch_bounds__(kFlopThreads) k_flop_pred(FlopArgs a) {
         }
       }
       const long long F = block_sum<kFlopThreads>(fpart, sm.red);
-      zm = (u128)hdr->z_acc * (u128)(unsigned long long)a.M;
-      den = (u128)(unsigned long long)F * (u128)hdr->s_acc;
-      ratio_ref = (F > 0 && !ref_empty) ? ((double)hdr->z_acc * (double)a.M) / ((double)F * (double)hdr->s_acc) : 0.0;
+      const unsigned long long S = hdr->s_acc;
+      const u128 zm = (u128)zz * (u128)(unsigned long long)a.M;
+      const u128 den = (u128)(unsigned long long)F * (u128)S;
+      const double ratio_ref = (F > 0 && S) ? ((double)zz * (double)a.M) / ((double)F * (double)S) : 0.0;
       long long pp = 0;
-      for (long long r = i0 + t; r < i1; r += kFlopThreads) {
+      for (int r = i0 + t; r < i1; r += kFlopThreads) {
         const int v = a.flop[r];
-        pp += ref_empty ? v : pred_reference((uint32_t)v, zm, den, ratio_ref, &sat);
+        const int p = S == 0 ? v : pred_reference((uint32_t)v, zm, den, ratio_ref, &sat);
+        a.pred[r] = p;
+        pp += p;
       }
       blk_p = block_sum<kFlopThreads>(pp, sm.red);
     }
@@ -271,32 +393,22 @@ __global__ void __launch_bounds__(kFlopThreads) k_flop_pred(FlopArgs a) {
     }
     long long run = block_sum<kFlopThreads>(ppart, sm.red);
 
-    // ---- phase 2: predictions and offsets of the owned rows [i0, i1)
-    for (long long rb = i0; rb < i1; rb += (long long)kFlopThreads * kRowsPerThread) {
-      const long long r0 = rb + (long long)t * kRowsPerThread;
+    // ---- phase 2: offsets of the owned rows [i0, i1)
+    for (int rb = i0; rb < i1; rb += kFlopThreads * kRowsPerThread) {
+      const int r0 = rb + t * kRowsPerThread;
       int pv[kRowsPerThread];
       long long loc = 0;
 #pragma unroll
       for (int u = 0; u < kRowsPerThread; ++u) {
-        const long long r = r0 + u;
-        pv[u] = 0;
-        if (r < i1) {
-          const int v = a.flop[r];
-          if (MODE == kModePredict)
-            pv[u] = (hdr->f_acc == 0) ? v : pred_proposed((uint32_t)v, hdr->z_acc, hdr->f_acc, ratio);
-          else
-            pv[u] = ref_empty ? v : pred_reference((uint32_t)v, zm, den, ratio_ref, &sat);
-          loc += pv[u];
-        }
+        pv[u] = (r0 + u < i1) ? a.pred[r0 + u] : 0;
+        loc += pv[u];
       }
       long long tot;
       long long ex = block_excl_scan<kFlopThreads>(loc, sm.red, &tot) + run;
 #pragma unroll
       for (int u = 0; u < kRowsPerThread; ++u) {
-        const long long r = r0 + u;
-        if (r < i1) {
-          a.pred[r] = pv[u];
-          a.offsets[r] = ex;
+        if (r0 + u < i1) {
+          a.offsets[r0 + u] = ex;
           ex += pv[u];
         }
       }
