@@ -5,39 +5,39 @@
 // Work split: the rows' end markers and A's nonzeros form one merged sequence
 // of M + nnz(A) items (the merge-path decomposition of Merrill and Garland,
 // "Merge-based parallel sparse matrix-vector multiplication", SC 2016).  Block
-// c takes the items [c*D/G, (c+1)*D/G), so every block reads the same number of
-// nonzeros plus row ends, whatever the row-length skew.  A row owned by block c
-// is one whose end marker lies in c's range; the part of a row that started in
-// an earlier block arrives as a carry published by that block.
+// c takes the items [c*D/G, (c+1)*D/G) and splits them again, evenly, among
+// its warps, so every warp reads the same number of nonzeros plus row ends,
+// whatever the row-length skew.  A row belongs to the warp (and block) holding
+// its end marker; the part of a row that started in an earlier warp or block
+// is carried over.
 //
-// Inside a block, A's nonzeros are taken kChunk at a time (the chunk grid is
-// aligned to 16 bytes, so every thread reads its kItems consecutive column ids
-// with two 128-bit loads, issued one chunk ahead).  Each nonzero's B row length
-// comes from one 128-bit load around B.rpt[c] (a second load only when the pair
-// straddles it); the lengths go to shared memory.  Then one thread per row sums
-// its row's segment of the chunk (segments longer than kLong are summed by
-// whole warps), into per-row sums of the current window of kWin rows, whose end
-// offsets sit in shared memory.  When a window's rows are complete it is
-// emitted: the prediction of each row is computed once and written.
-//
-// All blocks are co-resident (the grid never exceeds what the device holds at
-// once).  Blocks exchange three things through flags in the workspace, each
-// wait bounded: the carry of a row that spans blocks, the block's total of
-// predicted nnz (for the scan), and, in the reference design, the block's FLOP
-// total (F is needed before any prediction).
+// Each warp streams its range on its own, with no block-wide barrier: per step
+// it reads kSub column ids with fully coalesced 128-bit loads (issued one step
+// ahead), fetches each nonzero's B row length with one 128-bit load around
+// B.rpt[c] (a second load only when the pair straddles it), stages the lengths
+// in a warp-private shared buffer, and sums them per row: lane l owns row
+// rbase + l of a 32-row window whose end offsets it holds in a register;
+// segments longer than kLong are summed by the whole warp.  When the window's
+// rows are complete the warp writes their predictions (computed once per row)
+// and moves on.  After the stream, one thread joins the rows split between
+// warps, then blocks exchange, through flags in the workspace with bounded
+// waits: the carry of a row that spans blocks, the block's total of predicted
+// nnz (for the scan), and, in the reference design, the block's FLOP total (F
+// is needed before any prediction).  All blocks are co-resident (the grid
+// never exceeds what the device holds at once).
 #pragma once
 
 #include "common.cuh"
 
 namespace spg {
 
-constexpr int kFlopThreads = 512;
-constexpr int kItems = 8;                       // nonzeros per thread per chunk
-constexpr int kChunk = kFlopThreads * kItems;   // nonzeros per chunk
-constexpr int kWin = 2048;                      // rows per window
-constexpr int kLong = 64;                       // longer row segments are summed by warps
-constexpr int kMaxLong = kChunk / kLong + 1;
+constexpr int kFlopThreads = 256;
+constexpr int kFlopWarps = kFlopThreads / 32;
+constexpr int kLaneItems = 8;                   // nonzeros per lane per step
+constexpr int kSub = 32 * kLaneItems;           // nonzeros per warp step
+constexpr int kLong = 48;                       // longer row segments are summed by the warp
 constexpr int kRowsPerThread = 4;               // rows per thread in the offsets pass
+constexpr int kNoEnd = 0x7fffffff;
 
 enum FlopMode { kModeFlop = 0, kModePredict = 1, kModeReference = 2 };
 
@@ -54,55 +54,44 @@ struct FlopArgs {
   spgemm_result_t* res;
 };
 
-// Number of row ends among the first d items of the merged sequence: the
-// largest i in [0, M] with i == 0 or rpt[i] + i <= d.  One warp, 32-way search.
-__device__ long long merge_path_rows(const int* rpt, long long M, long long d) {
+// Number of row ends among the first d items of the merged sequence, searched
+// in [lo, hi): the largest i in [lo, hi) with i == 0 or rpt[i] + i <= d, given
+// that the predicate holds at lo and fails at hi.  One warp, 32-way search.
+__device__ long long merge_path_rows(const int* rpt, long long lo, long long hi, long long d) {
   const int lane = threadIdx.x & 31;
-  long long lo = 0, hi = M + 1;  // predicate true at lo, false at hi
   while (hi - lo > 1) {
     const long long step = (hi - lo + 31) / 32;
     const long long x = lo + (long long)(lane + 1) * step;
     bool pr = false;
     if (x < hi) pr = (long long)__ldg(rpt + x) + x <= d;
     const unsigned b = __ballot_sync(kFull, pr);
-    // predicate is monotone, so the true lanes form a prefix
-    const int cnt = __popc(b);
-    const long long nlo = lo + (long long)cnt * step;
+    // the predicate is monotone, so the true lanes form a prefix
+    const long long nlo = lo + (long long)__popc(b) * step;
     hi = min(hi, nlo + step);
     lo = nlo;
   }
   return lo;
 }
 
+// What a warp leaves for the block after its stream.
+struct WarpInfo {
+  int first_row;    // the warp's first row
+  int has_end;      // the warp holds at least one row end
+  int head_split;   // its first row started before the warp's range
+  int head_part;    // that row's partial FLOP within the warp (when it also ends here)
+  int tail_part;    // partial FLOP of the row open at the warp's end
+  int pad[3];
+};
+
 struct FlopShared {
-  alignas(16) int lbuf[kChunk];  // B row lengths of the chunk's nonzeros
-  int ends[kWin];    // end offset of each window row (clamped to the block's range)
-  int fsum[kWin];    // per-row FLOP of the window rows
-  int long_k[kMaxLong], long_a[kMaxLong], long_b[kMaxLong];
-  int long_n;
-  int win_js;        // first nonzero of the window's first row (clamped)
-  long long red[kFlopThreads / 32 + 1];
+  alignas(16) int lens[kFlopWarps][kSub];  // B row lengths of each warp's current step
+  WarpInfo info[kFlopWarps];
+  long long red[kFlopWarps + 1];
   long long bc[8];
 };
 
-// First index k in [lo, n) with v[k] >= key, or n.
-__device__ __forceinline__ int lower_bound_smem(const int* v, int lo, int n, int key) {
-  int hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (v[mid] < key) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-// B row length of column id c, with bounds checks; one 128-bit load when possible.
-struct LenLoad {
-  int4 v;
-  int extra;
-};
-
 template <int MODE>
-__global__ void __launch_bounds__(kFlopThreads, 2) k_flop_pred(FlopArgs a) {
+__global__ void __launch_bounds__(kFlopThreads, 4) k_flop_pred(FlopArgs a) {
   __shared__ FlopShared sm;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int G = gridDim.x, c = blockIdx.x;
@@ -110,55 +99,65 @@ __global__ void __launch_bounds__(kFlopThreads, 2) k_flop_pred(FlopArgs a) {
   const unsigned ep = *reinterpret_cast<volatile unsigned*>(&hdr->epoch) + 1u;
   Slot* slots = a.ws.slots;
   const int K = (int)a.K;
-
-  // ---- this block's share of the merged sequence
-  const long long D = a.M + a.nnzA;
-  if (warp == 0) {
-    const long long d0 = (long long)c * D / G, d1 = (long long)(c + 1) * D / G;
-    const long long i0 = merge_path_rows(a.a_rpt, a.M, d0);
-    const long long i1 = merge_path_rows(a.a_rpt, a.M, d1);
-    if (lane == 0) {
-      sm.bc[0] = i0;
-      sm.bc[1] = min(max(d0 - i0, 0ll), (long long)a.nnzA);
-      sm.bc[2] = i1;
-      sm.bc[3] = min(max(d1 - i1, 0ll), (long long)a.nnzA);
-    }
-  }
-  if (t == 0) sm.long_n = 0;
-  __syncthreads();
-  const int i0 = (int)sm.bc[0], j0 = (int)sm.bc[1], i1 = (int)sm.bc[2];
-  const int j1 = (int)max(sm.bc[3], sm.bc[1]);
-  const bool tail_row = i1 < a.M;  // row i1 continues into the next block
-  const int r_end = tail_row ? i1 + 1 : i1;
-  const bool head_split = (i0 < a.M) && (c > 0) && (__ldg(a.a_rpt + i0) < j0);
-
-  bool bad = false;
+  const int M = (int)a.M;
   const unsigned long long fz = hdr->f_acc, zz = hdr->z_acc;
   const double ratio = (MODE == kModePredict && fz) ? (double)zz / (double)fz : 0.0;
-  long long ftot = 0, ptot = 0;  // per-thread sums over complete rows
-  long long head_part = 0, tail_part = 0;
 
-  // ---- window of rows [wa, wa + nw)
-  int wa = i0, nw = 0;
-  auto load_window = [&](int start) {
-    wa = start;
-    nw = min(kWin, r_end - wa);
-    for (int k = t; k < nw; k += kFlopThreads) {
-      const int r = wa + k;
-      int e = (tail_row && r == i1) ? j1 : __ldg(a.a_rpt + r + 1);
-      e = min(max(e, j0), j1);
-      sm.ends[k] = e;
-      sm.fsum[k] = 0;
+  // ---- this block's share of the merged sequence, then this warp's share
+  const long long D = a.M + a.nnzA;
+  const long long d0 = (long long)c * D / G, d1 = (long long)(c + 1) * D / G;
+  if (warp == 0) {
+    const long long i0 = merge_path_rows(a.a_rpt, 0, a.M + 1, d0);
+    const long long i1 = merge_path_rows(a.a_rpt, 0, a.M + 1, d1);
+    if (lane == 0) {
+      sm.bc[0] = i0;
+      sm.bc[1] = i1;
     }
-    if (t == 0) sm.win_js = min(max(__ldg(a.a_rpt + wa), j0), j1);
+  }
+  __syncthreads();
+  const long long bi0 = sm.bc[0], bi1 = sm.bc[1];
+  const int i0 = (int)bi0, i1 = (int)bi1;
+  const int j0 = (int)min(max(d0 - bi0, 0ll), (long long)a.nnzA);
+  const int j1 = (int)max(min(max(d1 - bi1, 0ll), (long long)a.nnzA), (long long)j0);
+  const long long wd0 = d0 + (d1 - d0) * warp / kFlopWarps;
+  const long long wd1 = d0 + (d1 - d0) * (warp + 1) / kFlopWarps;
+  const long long wl0 = merge_path_rows(a.a_rpt, bi0, bi1 + 1, wd0);
+  const long long wl1 = merge_path_rows(a.a_rpt, bi0, bi1 + 1, wd1);
+  const int wi0 = (int)wl0, wi1 = (int)wl1;
+  const int wj0 = (int)min(max(wd0 - wl0, (long long)j0), (long long)j1);
+  const int wj1 = (int)min(max(wd1 - wl1, (long long)wj0), (long long)j1);
+  const bool wtail = wi1 < M;                 // row wi1 continues past this warp
+  const int rows_hi = wtail ? wi1 + 1 : wi1;  // rows touched: [wi0, rows_hi)
+  const bool whead = wi0 < M && __ldg(a.a_rpt + wi0) < wj0;  // first row started earlier
+
+  bool bad = false;
+  long long ftot = 0, ptot = 0;  // per-lane sums over rows this warp completes
+  int head_part = 0, tail_part = 0;
+  int* lw = sm.lens[warp];
+
+  // ---- the 32-row window [rbase, rbase + 32): lane l holds row rbase + l's end
+  int rbase = wi0;
+  int e_l = kNoEnd, st_l = 0;
+  auto load_rows = [&](int rb, int start_of_rb) {
+    rbase = rb;
+    const int r = rb + lane;
+    if (r < rows_hi) {
+      const int e = (wtail && r == wi1) ? wj1 : __ldg(a.a_rpt + r + 1);
+      e_l = min(max(e, wj0), wj1);
+    } else {
+      e_l = kNoEnd;
+    }
+    const int prev = __shfl_up_sync(kFull, e_l, 1);
+    st_l = lane == 0 ? start_of_rb : prev;
   };
-  auto emit_window = [&]() {
-    for (int k = t; k < nw; k += kFlopThreads) {
-      const int r = wa + k;
-      const int v = sm.fsum[k];
-      if (tail_row && r == i1) {
-        tail_part = v;  // seen by one thread only
-      } else if (head_split && r == i0) {
+  int acc = 0;
+  auto emit_rows = [&]() {
+    const int r = rbase + lane;
+    if (r < rows_hi) {
+      const int v = acc;
+      if (wtail && r == wi1) {
+        tail_part = v;
+      } else if (whead && r == wi0) {
         head_part = v;
       } else {
         ftot += v;
@@ -172,174 +171,194 @@ __global__ void __launch_bounds__(kFlopThreads, 2) k_flop_pred(FlopArgs a) {
         }
       }
     }
+    acc = 0;
   };
 
-  // ---- column ids of this thread's items of a chunk, as two 128-bit loads
-  auto load_cols = [&](int cs, int* col) {
-    const int q0 = cs + t * kItems;
-    if (a.vec_ok && (long long)q0 + kItems <= a.nnzA && q0 >= 0) {
-      const int4 x = __ldg(reinterpret_cast<const int4*>(a.a_col + q0));
-      const int4 y = __ldg(reinterpret_cast<const int4*>(a.a_col + q0 + 4));
-      col[0] = x.x; col[1] = x.y; col[2] = x.z; col[3] = x.w;
-      col[4] = y.x; col[5] = y.y; col[6] = y.z; col[7] = y.w;
-    } else {
+  load_rows(wi0, min(max(wi0 < M ? __ldg(a.a_rpt + wi0) : wj0, wj0), wj1));
+
+  // ---- column ids of a step: lane l takes [s + 4l, s + 4l + 4) and the same +128
+  auto load_cols = [&](int s, int* col) {
 #pragma unroll
-      for (int u = 0; u < kItems; ++u) {
-        const int q = q0 + u;
-        col[u] = (q >= 0 && q < a.nnzA) ? __ldg(a.a_col + q) : 0;
+    for (int h = 0; h < kLaneItems / 4; ++h) {
+      const int q0 = s + 4 * lane + 128 * h;
+      if (a.vec_ok && q0 >= 0 && (long long)q0 + 4 <= a.nnzA) {
+        const int4 x = __ldg(reinterpret_cast<const int4*>(a.a_col + q0));
+        col[4 * h] = x.x;
+        col[4 * h + 1] = x.y;
+        col[4 * h + 2] = x.z;
+        col[4 * h + 3] = x.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + u;
+          col[4 * h + u] = (q >= 0 && q < a.nnzA) ? __ldg(a.a_col + q) : 0;
+        }
       }
     }
   };
 
-  load_window(i0);
-  const int cs0 = j0 & ~3;
-  int col[kItems];
-  if (cs0 < j1) load_cols(cs0, col);
-  int ka = 0;
-  __syncthreads();
+  const int s0 = wj0 & ~3;
+  int col[kLaneItems];
+  if (s0 < wj1) load_cols(s0, col);
 
-  // ---- phase 1: FLOP of every row touching this block's items
-  for (int cs = cs0; cs < j1; cs += kChunk) {
-    const int lo = max(cs, j0), hi = min(cs + kChunk, j1);
-    // B row lengths of this thread's items, gathers issued four at a time
-    int len[kItems];
+  for (int s = s0; s < wj1; s += kSub) {
+    const int lo = max(s, wj0), hi = min(s + kSub, wj1);
+    // B row lengths, four gathers in flight per lane at a time
 #pragma unroll
-    for (int h = 0; h < kItems; h += 4) {
-      LenLoad ld[4];
+    for (int h = 0; h < kLaneItems / 4; ++h) {
+      int4 v[4];
+      int extra[4];
       bool use[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int q = cs + t * kItems + h + u;
-        const int cc = col[h + u];
+        const int q = s + 4 * lane + 128 * h + u;
+        const int cc = col[4 * h + u];
         use[u] = q >= lo && q < hi;
-        ld[u].v = make_int4(0, 0, 0, 0);
-        ld[u].extra = 0;
+        v[u] = make_int4(0, 0, 0, 0);
+        extra[u] = 0;
         if (use[u]) {
           if ((unsigned)cc >= (unsigned)K) {
             bad = true;
             use[u] = false;
           } else if (a.vec_ok && (cc | 3) <= K) {
-            ld[u].v = __ldg(reinterpret_cast<const int4*>(a.b_rpt) + (cc >> 2));
-            if ((cc & 3) == 3) ld[u].extra = __ldg(a.b_rpt + cc + 1);
+            v[u] = __ldg(reinterpret_cast<const int4*>(a.b_rpt) + (cc >> 2));
+            if ((cc & 3) == 3) extra[u] = __ldg(a.b_rpt + cc + 1);
           } else {
-            ld[u].v.x = __ldg(a.b_rpt + cc);
-            ld[u].v.y = __ldg(a.b_rpt + cc + 1);
+            v[u].x = __ldg(a.b_rpt + cc);
+            v[u].y = __ldg(a.b_rpt + cc + 1);
           }
         }
       }
+      int len[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int cc = col[h + u];
+        const int cc = col[4 * h + u];
         int b0, b1;
         if (a.vec_ok && (cc | 3) <= K) {
           const int r = cc & 3;
-          b0 = r == 0 ? ld[u].v.x : r == 1 ? ld[u].v.y : r == 2 ? ld[u].v.z : ld[u].v.w;
-          b1 = r == 0 ? ld[u].v.y : r == 1 ? ld[u].v.z : r == 2 ? ld[u].v.w : ld[u].extra;
+          b0 = r == 0 ? v[u].x : r == 1 ? v[u].y : r == 2 ? v[u].z : v[u].w;
+          b1 = r == 0 ? v[u].y : r == 1 ? v[u].z : r == 2 ? v[u].w : extra[u];
         } else {
-          b0 = ld[u].v.x;
-          b1 = ld[u].v.y;
+          b0 = v[u].x;
+          b1 = v[u].y;
         }
         int l = b1 - b0;
         if (use[u] && (l < 0 || b0 < 0 || (long long)b1 > a.nnzB)) {
           bad = true;
           l = 0;
         }
-        len[h + u] = use[u] ? l : 0;
+        len[u] = use[u] ? l : 0;
       }
+      *reinterpret_cast<int4*>(lw + 4 * lane + 128 * h) = make_int4(len[0], len[1], len[2], len[3]);
     }
-    {
-      // prefetch the next chunk's column ids
-      if (cs + kChunk < j1) load_cols(cs + kChunk, col);
-      int4* lb = reinterpret_cast<int4*>(sm.lbuf + t * kItems);
-      lb[0] = make_int4(len[0], len[1], len[2], len[3]);
-      lb[1] = make_int4(len[4], len[5], len[6], len[7]);
-    }
-    __syncthreads();
-    // one thread per row of the window overlapping [pos, hi)
-    int pos = lo;
+    if (s + kSub < wj1) load_cols(s + kSub, col);  // next step's ids, in flight during the sums
+    __syncwarp();
+
+    // per-row sums over [lo, hi); the window moves on while its rows complete
     for (;;) {
-      const int kb = lower_bound_smem(sm.ends, ka, nw, hi);  // first row ending at or after hi
-      const int kend = min(kb, nw - 1);
-      for (int k = ka + t; k <= kend; k += kFlopThreads) {
-        const int rs = k == 0 ? sm.win_js : sm.ends[k - 1];
-        const int sa = max(rs, pos), sb = min(sm.ends[k], hi);
-        if (sb - sa > kLong) {
-          const int e = atomicAdd(&sm.long_n, 1);
-          sm.long_k[e] = k;
-          sm.long_a[e] = sa;
-          sm.long_b[e] = sb;
-        } else {
-          int acc = 0;
-          for (int q = sa; q < sb; ++q) acc += sm.lbuf[q - cs];
-          sm.fsum[k] += acc;
-        }
+      const bool mine = rbase + lane < rows_hi;
+      const int sa = max(st_l, lo), sb = min(e_l, hi);
+      const bool lng = mine && sb - sa > kLong;
+      if (mine && !lng) {
+        for (int q = sa; q < sb; ++q) acc += lw[q - s];
       }
-      __syncthreads();
-      const int nl = sm.long_n;
-      if (nl) {
-        for (int e = 0; e < nl; ++e) {
-          const int sa = sm.long_a[e], sb = sm.long_b[e];
-          int acc = 0;
-          for (int q = sa + t; q < sb; q += kFlopThreads) acc += sm.lbuf[q - cs];
-          acc = warp_sum(acc);
-          if (lane == 0 && acc) atomicAdd(&sm.fsum[sm.long_k[e]], acc);
-        }
-        __syncthreads();
-        if (t == 0) sm.long_n = 0;
+      unsigned lm = __ballot_sync(kFull, lng);
+      while (lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1;
+        const int a0 = __shfl_sync(kFull, sa, src), b0 = __shfl_sync(kFull, sb, src);
+        int part = 0;
+        for (int q = a0 + lane; q < b0; q += 32) part += lw[q - s];
+        part = warp_sum(part);
+        if (lane == src) acc += part;
       }
-      if (kb < nw) {
-        ka = kend;
-        break;
-      }
-      // every row of the window ends before hi: emit it, move to the next rows
-      emit_window();
-      __syncthreads();
-      load_window(wa + nw);
-      __syncthreads();
-      pos = sm.win_js;
-      ka = 0;
-      if (nw <= 0) break;
+      const int ll = min(31, rows_hi - 1 - rbase);
+      const int last_end = __shfl_sync(kFull, e_l, ll);
+      if (last_end > hi || rbase + 32 >= rows_hi) break;  // rows continue into the next step
+      // all 32 rows of the window end within this step
+      emit_rows();
+      load_rows(rbase + 32, last_end);
     }
+    __syncwarp();
   }
-  // rows left after the last nonzero (the last window and trailing empty rows)
-  if (nw > 0) emit_window();
-  __syncthreads();
-  while (wa + nw < r_end) {
-    load_window(wa + nw);
-    __syncthreads();
-    emit_window();
-    __syncthreads();
+  // rows left after the last nonzero: the current window, then empty rows
+  emit_rows();
+  while (rbase + 32 < rows_hi) {
+    const int last_end = __shfl_sync(kFull, e_l, 31);
+    load_rows(rbase + 32, last_end);
+    emit_rows();
   }
 
-  // gather the per-thread head/tail parts (each was set by at most one thread)
-  const long long head_sum = block_sum<kFlopThreads>(head_part, sm.red);
-  const long long tail_sum = block_sum<kFlopThreads>(tail_part, sm.red);
+  // ---- per-warp summary for the block
+  tail_part = __reduce_add_sync(kFull, tail_part);
+  head_part = __reduce_add_sync(kFull, head_part);
+  if (lane == 0) {
+    WarpInfo& w = sm.info[warp];
+    w.first_row = wi0;
+    w.has_end = wi1 > wi0;
+    w.head_split = whead;
+    w.head_part = head_part;
+    w.tail_part = tail_part;
+  }
+  const bool blk_head_split = (i0 < M) && (c > 0) && (__ldg(a.a_rpt + i0) < j0);
   if (__syncthreads_or(bad) && t == 0) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
 
-  // ---- carry of rows spanning blocks (thread 0; waits only on block c-1)
+  // ---- rows split between warps (thread 0).  Only the block's first row can
+  // depend on the carry from the previous block.
   if (t == 0) {
+    long long run = 0;          // partial of the open row entering warp w
+    bool dep = blk_head_split;  // ... plus the previous block's carry
+    long long head_known = 0;   // block's first row: everything but the carry
+    bool head_pending = false;
     long long extra_f = 0, extra_p = 0;
-    if (head_split && i0 == i1) {
+    for (int w = 0; w < kFlopWarps; ++w) {
+      const WarpInfo& in = sm.info[w];
+      if (!in.has_end) {
+        run += in.tail_part;
+        continue;
+      }
+      if (in.head_split) {
+        const long long v = run + in.head_part;
+        if (dep) {
+          head_known = v;
+          head_pending = true;
+        } else {
+          extra_f += v;
+          if (MODE == kModePredict) {
+            const int p = fz == 0 ? (int)v : pred_proposed((uint32_t)v, zz, fz, ratio);
+            a.pred[in.first_row] = p;
+            if (a.flop) a.flop[in.first_row] = (int)v;
+            extra_p += p;
+          } else {
+            a.flop[in.first_row] = (int)v;
+          }
+        }
+      }
+      dep = false;
+      run = in.tail_part;
+    }
+    // carries between blocks (waits only on block c-1)
+    if (dep) {
       // the whole block lies inside one row: pass the carry on
       long long cin = 0;
       if (flag_wait(&slots[c - 1].carry_flag, ep, &hdr->status)) cin = slots[c - 1].carry;
-      slots[c].carry = cin + tail_sum;
+      slots[c].carry = cin + run;
       flag_store(&slots[c].carry_flag, ep);
     } else {
-      slots[c].carry = tail_row ? tail_sum : 0;
+      slots[c].carry = i1 < M ? run : 0;
       flag_store(&slots[c].carry_flag, ep);
-      if (head_split) {
+      if (head_pending) {
         long long cin = 0;
         if (flag_wait(&slots[c - 1].carry_flag, ep, &hdr->status)) cin = slots[c - 1].carry;
-        const long long v0 = cin + head_sum;
-        extra_f = v0;
+        const long long v = cin + head_known;
+        extra_f += v;
         if (MODE == kModePredict) {
-          const int p = fz == 0 ? (int)v0 : pred_proposed((uint32_t)v0, zz, fz, ratio);
+          const int p = fz == 0 ? (int)v : pred_proposed((uint32_t)v, zz, fz, ratio);
           a.pred[i0] = p;
-          if (a.flop) a.flop[i0] = (int)v0;
-          extra_p = p;
+          if (a.flop) a.flop[i0] = (int)v;
+          extra_p += p;
         } else {
-          a.flop[i0] = (int)v0;
+          a.flop[i0] = (int)v;
         }
       }
     }
