@@ -49,8 +49,8 @@ extern "C" {
 #define SPGEMM_ERR_WORKSPACE (-3)    /* ws_bytes < spgemm_workspace_size(A, B) */
 #define SPGEMM_ERR_CUDA (-4)         /* a CUDA launch or query failed */
 #define SPGEMM_ERR_TOO_LARGE (-5)    /* a size does not fit the int32 index range */
-#define SPGEMM_ERR_STATIC_CAPACITY (-6) /* spgemm_predict_structure_static: A.rows exceeds
-                                           SPGEMM_STATIC_MAX_ROWS */
+#define SPGEMM_ERR_STATIC_CAPACITY (-6) /* spgemm_predict_structure_static: A.rows or A.cols
+                                           exceeds SPGEMM_STATIC_MAX_ROWS */
 
 /* ---- device status bits (res->status) ------------------------------------------ */
 #define SPGEMM_STATUS_OK 0
@@ -115,8 +115,8 @@ typedef struct spgemm_result {
 /* ---- entry points ----------------------------------------------------------------- */
 
 /* Bytes of device workspace every entry point below needs for these operands
- * (about 8 * A.rows bytes plus a fixed 320 KB).  B may be NULL for
- * spgemm_sample_rows / spgemm_validate_csr. */
+ * (about 8 * A.rows + A.cols bytes plus a fixed 263 KB).  B may be NULL; the
+ * size depends on A's shape only. */
 size_t spgemm_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B);
 
 /* Algorithm 1 (Sec. V-A): flop_row[i] = sum over j in row i of A of
@@ -190,8 +190,9 @@ int spgemm_set_profile_events(void* before, void* after);
  * cudaMalloc because that call can synchronise the whole device.
  *
  * The scratch space is a fixed array of device memory compiled into the library,
- * sized for A.rows <= SPGEMM_STATIC_MAX_ROWS (about 17 MB).  Every GPU that loads
- * the library holds it until the process exits.  Larger problems are rejected
+ * sized for A.rows <= SPGEMM_STATIC_MAX_ROWS and A.cols <= SPGEMM_STATIC_MAX_ROWS
+ * (about 19 MB).  Every GPU that loads the library holds it until the process
+ * exits.  Larger problems are rejected
  * with SPGEMM_ERR_STATIC_CAPACITY before anything is queued.  The call allocates
  * nothing (no cudaMalloc/cudaFree, no allocating library routine): the caller
  * still passes the inputs, outputs and result record, as for

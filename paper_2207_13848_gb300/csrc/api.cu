@@ -15,6 +15,7 @@ using namespace spg;
 namespace {
 
 constexpr long long kIdxMax = 2147483647ll;
+constexpr int kDegThreads = 256;
 
 // Per-device launch limits, computed once per device.
 struct DeviceLimits {
@@ -92,7 +93,7 @@ int check_pair(const spgemm_csr_t* A, const spgemm_csr_t* B, void* ws, size_t ws
   if (!csr_ok(A) || !csr_ok(B) || !res || !ws) return SPGEMM_ERR_INVALID_ARG;
   if (A->cols != B->rows) return SPGEMM_ERR_DIM_MISMATCH;
   if (!csr_fits(A) || !csr_fits(B)) return SPGEMM_ERR_TOO_LARGE;
-  if (ws_bytes < ws_bytes_for(A->rows)) return SPGEMM_ERR_WORKSPACE;
+  if (ws_bytes < ws_bytes_for(A->rows, A->cols)) return SPGEMM_ERR_WORKSPACE;
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return SPGEMM_ERR_WORKSPACE;
   return SPGEMM_OK;
 }
@@ -170,6 +171,7 @@ FlopArgs flop_args(const spgemm_csr_t* A, const spgemm_csr_t* B, const Workspace
   f.a_rpt = A->rpt;
   f.a_col = A->col;
   f.b_rpt = B->rpt;
+  f.deg8 = w.deg8;
   f.flop = flop ? flop : (flop_optional ? nullptr : w.flop_buf);
   f.vec_ok = ((reinterpret_cast<uintptr_t>(A->col) | reinterpret_cast<uintptr_t>(B->rpt)) & 15) == 0;
   f.pred = pred;
@@ -181,6 +183,10 @@ FlopArgs flop_args(const spgemm_csr_t* A, const spgemm_csr_t* B, const Workspace
 
 template <int MODE>
 int launch_flop(const DeviceLimits* L, const FlopArgs& f, cudaStream_t st) {
+  if (f.K > 0) {
+    const int gd = grid_for((f.K + 3) / 4, kDegThreads, (long long)L->sms * 8);
+    k_degree_table<<<gd, kDegThreads, 0, st>>>(f.b_rpt, f.K, f.nnzB, f.ws.deg8, f.ws.hdr);
+  }
   const long long D = f.M + f.nnzA;
   const int g = grid_for(D, 4096, (long long)L->sms * L->flop_blocks_per_sm);
   prof_mark(false, st);
@@ -220,13 +226,14 @@ int predict_common(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_co
 }
 
 // ---- scratch for spgemm_predict_structure_static --------------------------------
-// The workspace of a problem with SPGEMM_STATIC_MAX_ROWS rows, as one file-scope
+// The workspace of a problem with SPGEMM_STATIC_MAX_ROWS rows and columns in A, as one file-scope
 // device array.  In host code the name is only a stand-in for the device
 // object: its device address comes from cudaGetSymbolAddress, looked up once per
 // device below and passed to the kernels.
 constexpr size_t kStaticHeaderBytes = sizeof(WsHeader) + sizeof(Slot) * kMaxSlots;
 constexpr size_t kStaticRowBytes = ((size_t)SPGEMM_STATIC_MAX_ROWS * 4 + 255) / 256 * 256;
-constexpr size_t kStaticBytes = kStaticHeaderBytes + 2 * kStaticRowBytes;
+constexpr size_t kStaticDegBytes = ((size_t)SPGEMM_STATIC_MAX_ROWS + 16 + 255) / 256 * 256;
+constexpr size_t kStaticBytes = kStaticHeaderBytes + 2 * kStaticRowBytes + kStaticDegBytes;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 void* g_static_ptr[kMaxDevices];
@@ -246,7 +253,7 @@ extern "C" {
 size_t spgemm_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B) {
   (void)B;
   if (!A || A->rows < 0) return 0;
-  return ws_bytes_for(A->rows);
+  return ws_bytes_for(A->rows, A->cols);
 }
 
 int spgemm_flop_per_row(const spgemm_csr_t* A, const spgemm_csr_t* B, int32_t* flop_row,
@@ -316,7 +323,7 @@ int spgemm_sample_rows(int64_t rows, const spgemm_config_t* cfg, int32_t* ids, i
                        spgemm_result_t* res, void* ws, size_t ws_bytes, void* stream) {
   if (rows < 0 || rows >= kIdxMax || !res || !ws || capacity < 0 || (capacity > 0 && !ids))
     return SPGEMM_ERR_INVALID_ARG;
-  if (ws_bytes < ws_bytes_for(rows) || (reinterpret_cast<uintptr_t>(ws) & 255)) return SPGEMM_ERR_WORKSPACE;
+  if (ws_bytes < ws_bytes_for(rows, 0) || (reinterpret_cast<uintptr_t>(ws) & 255)) return SPGEMM_ERR_WORKSPACE;
   long long n_cand = 0;
   int rc = sample_candidates(cfg, rows, &n_cand);
   if (rc) return rc;
@@ -332,7 +339,7 @@ int spgemm_validate_csr(const spgemm_csr_t* A, spgemm_result_t* res, void* ws, s
                         void* stream) {
   if (!csr_ok(A) || !res || !ws) return SPGEMM_ERR_INVALID_ARG;
   if (!csr_fits(A)) return SPGEMM_ERR_TOO_LARGE;
-  if (ws_bytes < ws_bytes_for(A->rows) || (reinterpret_cast<uintptr_t>(ws) & 255)) return SPGEMM_ERR_WORKSPACE;
+  if (ws_bytes < ws_bytes_for(A->rows, 0) || (reinterpret_cast<uintptr_t>(ws) & 255)) return SPGEMM_ERR_WORKSPACE;
   const DeviceLimits* L = limits();
   if (!L) return SPGEMM_ERR_CUDA;
   Workspace w = ws_carve(ws, A->rows);
@@ -346,13 +353,13 @@ int spgemm_predict_structure_static(const spgemm_csr_t* A, const spgemm_csr_t* B
                                     int64_t* offsets, int32_t* flop_row, spgemm_result_t* res,
                                     void* stream) {
   if (!csr_ok(A)) return SPGEMM_ERR_INVALID_ARG;
-  if (A->rows > SPGEMM_STATIC_MAX_ROWS) return SPGEMM_ERR_STATIC_CAPACITY;
+  if (A->rows > SPGEMM_STATIC_MAX_ROWS || A->cols > SPGEMM_STATIC_MAX_ROWS) return SPGEMM_ERR_STATIC_CAPACITY;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SPGEMM_ERR_CUDA;
   std::call_once(g_static_once[dev], init_static_scratch, dev);
   void* ws = g_static_ptr[dev];
   if (!ws) return SPGEMM_ERR_CUDA;
-  if (ws_bytes_for(A->rows) > kStaticBytes) return SPGEMM_ERR_STATIC_CAPACITY;
+  if (ws_bytes_for(A->rows, A->cols) > kStaticBytes) return SPGEMM_ERR_STATIC_CAPACITY;
   // Header, per-block slots and flag epoch start from zero on every call.
   if (cudaMemsetAsync(ws, 0, kStaticHeaderBytes, static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return SPGEMM_ERR_CUDA;
@@ -374,7 +381,7 @@ const char* spgemm_status_string(int code) {
     case SPGEMM_ERR_CUDA: return "CUDA launch or query failed";
     case SPGEMM_ERR_TOO_LARGE: return "size exceeds the int32 index range";
     case SPGEMM_ERR_STATIC_CAPACITY:
-      return "A.rows exceeds the static scratch of spgemm_predict_structure_static (SPGEMM_STATIC_MAX_ROWS)";
+      return "A.rows or A.cols exceeds the static scratch of spgemm_predict_structure_static (SPGEMM_STATIC_MAX_ROWS)";
     case SPGEMM_STATUS_WARN_EMPTY_SAMPLE: return "warning: empty sample, prediction fell back to FLOP";
     case SPGEMM_STATUS_WARN_SATURATED: return "warning: a prediction saturated at 2^31-1";
     case SPGEMM_STATUS_WARN_UNSORTED: return "warning: a row is not strictly increasing";

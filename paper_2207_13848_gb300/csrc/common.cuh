@@ -49,20 +49,24 @@ struct alignas(64) Slot {
 struct Workspace {
   WsHeader* hdr;
   Slot* slots;
-  int* heavy;     // [M] rows queued for the block-per-row deduplication
-  int* flop_buf;  // [M] per-row FLOP when the caller gives no flop_row buffer
+  int* heavy;            // [M] rows queued for the block-per-row deduplication
+  int* flop_buf;         // [M] per-row FLOP when the caller gives no flop_row buffer
+  unsigned char* deg8;   // [K] B row lengths capped at kDegEscape (see k_degree_table)
 };
 
-inline size_t ws_bytes_for(int64_t M) {
-  size_t m = (size_t)(M > 0 ? M : 1);
-  size_t b = sizeof(WsHeader) + sizeof(Slot) * kMaxSlots;
-  b += ((m * 4 + 255) / 256) * 256;  // heavy
-  b += ((m * 4 + 255) / 256) * 256;  // flop_buf
-  return b;
+// B row lengths of at least kDegEscape are read from B.rpt instead of the table.
+constexpr int kDegEscape = 255;
+
+inline size_t ws_round(size_t b) { return ((b + 255) / 256) * 256; }
+
+// Bytes for M rows of A and K columns of A (= rows of B).
+inline size_t ws_bytes_for(int64_t M, int64_t K) {
+  const size_t m = (size_t)(M > 0 ? M : 1), k = (size_t)(K > 0 ? K : 1);
+  return sizeof(WsHeader) + sizeof(Slot) * kMaxSlots + 2 * ws_round(m * 4) + ws_round(k + 16);
 }
 
 inline Workspace ws_carve(void* base, int64_t M) {
-  size_t m = (size_t)(M > 0 ? M : 1);
+  const size_t m = (size_t)(M > 0 ? M : 1);
   char* p = static_cast<char*>(base);
   Workspace w;
   w.hdr = reinterpret_cast<WsHeader*>(p);
@@ -70,8 +74,10 @@ inline Workspace ws_carve(void* base, int64_t M) {
   w.slots = reinterpret_cast<Slot*>(p);
   p += sizeof(Slot) * kMaxSlots;
   w.heavy = reinterpret_cast<int*>(p);
-  p += ((m * 4 + 255) / 256) * 256;
+  p += ws_round(m * 4);
   w.flop_buf = reinterpret_cast<int*>(p);
+  p += ws_round(m * 4);
+  w.deg8 = reinterpret_cast<unsigned char*>(p);
   return w;
 }
 
@@ -222,6 +228,35 @@ __device__ __noinline__ bool flag_wait(const unsigned int* p, unsigned int want,
 }
 
 __device__ __forceinline__ void set_status(WsHeader* h, unsigned bits) { atomicOr(&h->status, bits); }
+
+// Byte table of B's row lengths: deg8[k] = min(B.rpt[k+1] - B.rpt[k], kDegEscape).
+// Lookups into this 1-byte table replace the pair of B.rpt loads per nonzero
+// in the FLOP pass (fewer L2 sectors and more L1 reuse); kDegEscape means
+// "read B.rpt".  Offsets out of range give 0 and the bad-input status bit.
+__global__ void k_degree_table(const int* b_rpt, long long K, long long nnzB, unsigned char* deg8,
+                               WsHeader* hdr) {
+  bool bad = false;
+  const long long stride = (long long)gridDim.x * blockDim.x * 4;
+  for (long long k0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4; k0 < K; k0 += stride) {
+    unsigned word = 0;
+    long long prev = __ldg(b_rpt + k0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (k0 + u < K) {
+        const long long next = __ldg(b_rpt + k0 + u + 1);
+        long long d = next - prev;
+        if (d < 0 || prev < 0 || next > nnzB) {
+          bad = true;
+          d = 0;
+        }
+        word |= (unsigned)(d < kDegEscape ? d : kDegEscape) << (8 * u);
+        prev = next;
+      }
+    }
+    *reinterpret_cast<unsigned*>(deg8 + k0) = word;
+  }
+  if (bad) atomicOr(&hdr->status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
+}
 
 // Clamp a row range [b, e) read from untrusted offsets into [0, nnz].
 __device__ __forceinline__ bool clamp_range(long long& b, long long& e, long long nnz) {

@@ -13,14 +13,14 @@
 //
 // Each warp streams its range on its own, with no block-wide barrier: per step
 // it reads kSub column ids with fully coalesced 128-bit loads (issued one step
-// ahead), fetches each nonzero's B row length with one 128-bit load around
-// B.rpt[c] (a second load only when the pair straddles it), stages the lengths
-// in a warp-private shared buffer, and sums them per row: lane l owns row
-// rbase + l of a 32-row window whose end offsets it holds in a register;
-// segments longer than kLong are summed by the whole warp.  When the window's
-// rows are complete the warp writes their predictions (computed once per row)
-// and moves on.  After the stream, one thread joins the rows split between
-// warps, then blocks exchange, through flags in the workspace with bounded
+// ahead), looks up each nonzero's B row length in a byte table built per call
+// (k_degree_table; B.rpt only for lengths of 255 or more), and stores the
+// inclusive prefix sums of the step's lengths in a warp-private shared buffer.
+// Lane l owns row rbase + l of a 32-row window whose end offsets it holds in a
+// register; the row's share of the step is the difference of two prefix sums,
+// whatever its length.  When the window's rows are complete the warp writes
+// their predictions (computed once per row) and moves on.  After the stream,
+// one thread joins the rows split between warps, then blocks exchange, through flags in the workspace with bounded
 // waits: the carry of a row that spans blocks, the block's total of predicted
 // nnz (for the scan), and, in the reference design, the block's FLOP total (F
 // is needed before any prediction).  All blocks are co-resident (the grid
@@ -35,7 +35,6 @@ constexpr int kFlopThreads = 256;
 constexpr int kFlopWarps = kFlopThreads / 32;
 constexpr int kLaneItems = 8;                   // nonzeros per lane per step
 constexpr int kSub = 32 * kLaneItems;           // nonzeros per warp step
-constexpr int kLong = 48;                       // longer row segments are summed by the warp
 constexpr int kRowsPerThread = 4;               // rows per thread in the offsets pass
 constexpr int kNoEnd = 0x7fffffff;
 
@@ -46,6 +45,7 @@ struct FlopArgs {
   const int* a_rpt;
   const int* a_col;
   const int* b_rpt;
+  const unsigned char* deg8;  // [K] B row lengths capped at kDegEscape (k_degree_table)
   int* flop;             // [M] per-row FLOP: caller's flop_row, or null (predict) / workspace (others)
   int* pred;             // [M] per-row prediction (predict / reference)
   long long* offsets;    // [M + 1]
@@ -84,7 +84,7 @@ struct WarpInfo {
 };
 
 struct FlopShared {
-  alignas(16) int lens[kFlopWarps][kSub];  // B row lengths of each warp's current step
+  alignas(16) int lens[kFlopWarps][kSub];  // prefix sums of B row lengths over a warp's step
   WarpInfo info[kFlopWarps];
   long long red[kFlopWarps + 1];
   long long bc[8];
@@ -203,74 +203,51 @@ __global__ void __launch_bounds__(kFlopThreads, 4) k_flop_pred(FlopArgs a) {
 
   for (int s = s0; s < wj1; s += kSub) {
     const int lo = max(s, wj0), hi = min(s + kSub, wj1);
-    // B row lengths, four gathers in flight per lane at a time
+    // B row lengths from the byte table (B.rpt only for lengths >= kDegEscape),
+    // then their inclusive prefix sums over the step's kSub items (mod 2^32).
+    unsigned run_half = 0;
 #pragma unroll
     for (int h = 0; h < kLaneItems / 4; ++h) {
-      int4 v[4];
-      int extra[4];
-      bool use[4];
+      unsigned len[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int q = s + 4 * lane + 128 * h + u;
         const int cc = col[4 * h + u];
-        use[u] = q >= lo && q < hi;
-        v[u] = make_int4(0, 0, 0, 0);
-        extra[u] = 0;
-        if (use[u]) {
-          if ((unsigned)cc >= (unsigned)K) {
-            bad = true;
-            use[u] = false;
-          } else if (a.vec_ok && (cc | 3) <= K) {
-            v[u] = __ldg(reinterpret_cast<const int4*>(a.b_rpt) + (cc >> 2));
-            if ((cc & 3) == 3) extra[u] = __ldg(a.b_rpt + cc + 1);
+        len[u] = 0;
+        if (q >= lo && q < hi) {
+          if ((unsigned)cc < (unsigned)K) {
+            len[u] = __ldg(a.deg8 + cc);
           } else {
-            v[u].x = __ldg(a.b_rpt + cc);
-            v[u].y = __ldg(a.b_rpt + cc + 1);
+            bad = true;
           }
         }
       }
-      int len[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int cc = col[4 * h + u];
-        int b0, b1;
-        if (a.vec_ok && (cc | 3) <= K) {
-          const int r = cc & 3;
-          b0 = r == 0 ? v[u].x : r == 1 ? v[u].y : r == 2 ? v[u].z : v[u].w;
-          b1 = r == 0 ? v[u].y : r == 1 ? v[u].z : r == 2 ? v[u].w : extra[u];
-        } else {
-          b0 = v[u].x;
-          b1 = v[u].y;
+        if (len[u] == kDegEscape) {
+          const int cc = col[4 * h + u];
+          const int b0 = __ldg(a.b_rpt + cc), b1 = __ldg(a.b_rpt + cc + 1);
+          len[u] = (unsigned)(b1 - b0);  // validated by the table kernel
         }
-        int l = b1 - b0;
-        if (use[u] && (l < 0 || b0 < 0 || (long long)b1 > a.nnzB)) {
-          bad = true;
-          l = 0;
-        }
-        len[u] = use[u] ? l : 0;
       }
-      *reinterpret_cast<int4*>(lw + 4 * lane + 128 * h) = make_int4(len[0], len[1], len[2], len[3]);
+      const unsigned p0 = len[0], p1 = p0 + len[1], p2 = p1 + len[2], p3 = p2 + len[3];
+      const unsigned incl = warp_incl_scan(p3);
+      const unsigned base = run_half + incl - p3;
+      *reinterpret_cast<uint4*>(lw + 4 * lane + 128 * h) = make_uint4(base + p0, base + p1, base + p2, base + p3);
+      run_half += __shfl_sync(kFull, incl, 31);
     }
     if (s + kSub < wj1) load_cols(s + kSub, col);  // next step's ids, in flight during the sums
     __syncwarp();
 
-    // per-row sums over [lo, hi); the window moves on while its rows complete
+    // per-row sums over [lo, hi) from the prefix sums; the window moves on
+    // while its rows complete
     for (;;) {
       const bool mine = rbase + lane < rows_hi;
       const int sa = max(st_l, lo), sb = min(e_l, hi);
-      const bool lng = mine && sb - sa > kLong;
-      if (mine && !lng) {
-        for (int q = sa; q < sb; ++q) acc += lw[q - s];
-      }
-      unsigned lm = __ballot_sync(kFull, lng);
-      while (lm) {
-        const int src = __ffs(lm) - 1;
-        lm &= lm - 1;
-        const int a0 = __shfl_sync(kFull, sa, src), b0 = __shfl_sync(kFull, sb, src);
-        int part = 0;
-        for (int q = a0 + lane; q < b0; q += 32) part += lw[q - s];
-        part = warp_sum(part);
-        if (lane == src) acc += part;
+      if (mine && sb > sa) {
+        const unsigned pb = lw[sb - 1 - s];
+        const unsigned pa = sa > s ? (unsigned)lw[sa - 1 - s] : 0u;
+        acc += (int)(pb - pa);
       }
       const int ll = min(31, rows_hi - 1 - rbase);
       const int last_end = __shfl_sync(kFull, e_l, ll);
