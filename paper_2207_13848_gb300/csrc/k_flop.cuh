@@ -138,17 +138,24 @@ __global__ void __launch_bounds__(kFlopThreads, 4) k_flop_pred(FlopArgs a) {
   // ---- the 32-row window [rbase, rbase + 32): lane l holds row rbase + l's end
   int rbase = wi0;
   int e_l = kNoEnd, st_l = 0;
-  auto load_rows = [&](int rb, int start_of_rb) {
+  // raw end offset of this lane's row in the next window, loaded one window ahead
+  int e_next = 0;
+  auto fetch_next = [&](int rb) {
+    const int r = rb + lane;
+    e_next = (r < rows_hi && !(wtail && r == wi1)) ? __ldg(a.a_rpt + r + 1) : 0;
+  };
+  auto load_rows = [&](int rb, int start_of_rb) {  // rb's ends were fetched by fetch_next(rb)
     rbase = rb;
     const int r = rb + lane;
     if (r < rows_hi) {
-      const int e = (wtail && r == wi1) ? wj1 : __ldg(a.a_rpt + r + 1);
+      const int e = (wtail && r == wi1) ? wj1 : e_next;
       e_l = min(max(e, wj0), wj1);
     } else {
       e_l = kNoEnd;
     }
     const int prev = __shfl_up_sync(kFull, e_l, 1);
     st_l = lane == 0 ? start_of_rb : prev;
+    fetch_next(rb + 32);
   };
   int acc = 0;
   auto emit_rows = [&]() {
@@ -174,6 +181,7 @@ __global__ void __launch_bounds__(kFlopThreads, 4) k_flop_pred(FlopArgs a) {
     acc = 0;
   };
 
+  fetch_next(wi0);
   load_rows(wi0, min(max(wi0 < M ? __ldg(a.a_rpt + wi0) : wj0, wj0), wj1));
 
   // ---- column ids of a step: lane l takes [s + 4l, s + 4l + 4) and the same +128
@@ -205,32 +213,33 @@ __global__ void __launch_bounds__(kFlopThreads, 4) k_flop_pred(FlopArgs a) {
     const int lo = max(s, wj0), hi = min(s + kSub, wj1);
     // B row lengths from the byte table (B.rpt only for lengths >= kDegEscape),
     // then their inclusive prefix sums over the step's kSub items (mod 2^32).
+    unsigned len[kLaneItems];
+#pragma unroll
+    for (int u = 0; u < kLaneItems; ++u) {  // all of the lane's gathers in flight at once
+      const int q = s + 4 * lane + 128 * (u >> 2) + (u & 3);
+      const int cc = col[u];
+      len[u] = 0;
+      if (q >= lo && q < hi) {
+        if ((unsigned)cc < (unsigned)K) {
+          len[u] = __ldg(a.deg8 + cc);
+        } else {
+          bad = true;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kLaneItems; ++u) {
+      if (len[u] == kDegEscape) {
+        const int cc = col[u];
+        const int b0 = __ldg(a.b_rpt + cc), b1 = __ldg(a.b_rpt + cc + 1);
+        len[u] = (unsigned)(b1 - b0);  // validated by the table kernel
+      }
+    }
     unsigned run_half = 0;
 #pragma unroll
     for (int h = 0; h < kLaneItems / 4; ++h) {
-      unsigned len[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = s + 4 * lane + 128 * h + u;
-        const int cc = col[4 * h + u];
-        len[u] = 0;
-        if (q >= lo && q < hi) {
-          if ((unsigned)cc < (unsigned)K) {
-            len[u] = __ldg(a.deg8 + cc);
-          } else {
-            bad = true;
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (len[u] == kDegEscape) {
-          const int cc = col[4 * h + u];
-          const int b0 = __ldg(a.b_rpt + cc), b1 = __ldg(a.b_rpt + cc + 1);
-          len[u] = (unsigned)(b1 - b0);  // validated by the table kernel
-        }
-      }
-      const unsigned p0 = len[0], p1 = p0 + len[1], p2 = p1 + len[2], p3 = p2 + len[3];
+      const unsigned p0 = len[4 * h], p1 = p0 + len[4 * h + 1], p2 = p1 + len[4 * h + 2],
+                     p3 = p2 + len[4 * h + 3];
       const unsigned incl = warp_incl_scan(p3);
       const unsigned base = run_half + incl - p3;
       *reinterpret_cast<uint4*>(lw + 4 * lane + 128 * h) = make_uint4(base + p0, base + p1, base + p2, base + p3);
