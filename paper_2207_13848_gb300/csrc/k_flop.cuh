@@ -31,9 +31,20 @@
 
 namespace spg {
 
-constexpr int kFlopThreads = 256;
+// Build-time tuning knobs (defaults are the tuned values on GB300).
+#ifndef SPG_FLOP_THREADS
+#define SPG_FLOP_THREADS 256
+#endif
+#ifndef SPG_FLOP_MIN_BLOCKS
+#define SPG_FLOP_MIN_BLOCKS 4
+#endif
+#ifndef SPG_LANE_ITEMS
+#define SPG_LANE_ITEMS 8
+#endif
+
+constexpr int kFlopThreads = SPG_FLOP_THREADS;
 constexpr int kFlopWarps = kFlopThreads / 32;
-constexpr int kLaneItems = 8;                   // nonzeros per lane per step
+constexpr int kLaneItems = SPG_LANE_ITEMS;      // nonzeros per lane per step (multiple of 4)
 constexpr int kSub = 32 * kLaneItems;           // nonzeros per warp step
 constexpr int kRowsPerThread = 4;               // rows per thread in the offsets pass
 constexpr int kNoEnd = 0x7fffffff;
@@ -91,7 +102,7 @@ struct FlopShared {
 };
 
 template <int MODE>
-__global__ void __launch_bounds__(kFlopThreads, 4) k_flop_pred(FlopArgs a) {
+__global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) k_flop_pred(FlopArgs a) {
   __shared__ FlopShared sm;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int G = gridDim.x, c = blockIdx.x;
