@@ -65,23 +65,32 @@ struct FlopArgs {
   spgemm_result_t* res;
 };
 
-// Number of row ends among the first d items of the merged sequence, searched
-// in [lo, hi): the largest i in [lo, hi) with i == 0 or rpt[i] + i <= d, given
-// that the predicate holds at lo and fails at hi.  One warp, 32-way search.
-__device__ long long merge_path_rows(const int* rpt, long long lo, long long hi, long long d) {
-  const int lane = threadIdx.x & 31;
-  while (hi - lo > 1) {
-    const long long step = (hi - lo + 31) / 32;
-    const long long x = lo + (long long)(lane + 1) * step;
-    bool pr = false;
-    if (x < hi) pr = (long long)__ldg(rpt + x) + x <= d;
+// Number of row ends among the first d items of the merged sequence: the
+// largest i in [0, M] with i == 0 or rpt[i] + i <= d (the predicate is
+// monotone in i).  Two independent searches run at once, one per half-warp
+// (16-way each): iA for dA and iB for dB, both over the whole matrix.  Cuts the dependent loads of a block's set-up from two
+// nested searches to one.
+__device__ void merge_path_rows2(const int* rpt, long long M, long long dA, long long dB,
+                                 long long* iA, long long* iB) {
+  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+  const long long d = half ? dB : dA;
+  long long lo = 0, hi = M + 1;  // predicate true at lo, false at hi
+  for (;;) {
+    const bool active = hi - lo > 1;
+    if (!__any_sync(kFull, active)) break;
+    const long long step = (hi - lo + 15) / 16;
+    const long long x = lo + (long long)(hl + 1) * step;
+    const bool pr = active && x < hi && (long long)__ldg(rpt + x) + x <= d;
     const unsigned b = __ballot_sync(kFull, pr);
-    // the predicate is monotone, so the true lanes form a prefix
-    const long long nlo = lo + (long long)__popc(b) * step;
-    hi = min(hi, nlo + step);
-    lo = nlo;
+    const unsigned mine = half ? (b >> 16) : (b & 0xffffu);
+    if (active) {
+      const long long nlo = lo + (long long)__popc(mine) * step;
+      hi = min(hi, nlo + step);
+      lo = nlo;
+    }
   }
-  return lo;
+  *iA = __shfl_sync(kFull, lo, 0);
+  *iB = __shfl_sync(kFull, lo, 16);
 }
 
 // What a warp leaves for the block after its stream.
@@ -114,26 +123,22 @@ __global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) k_flop_pred
   const unsigned long long fz = hdr->f_acc, zz = hdr->z_acc;
   const double ratio = (MODE == kModePredict && fz) ? (double)zz / (double)fz : 0.0;
 
-  // ---- this block's share of the merged sequence, then this warp's share
+  // ---- this block's share of the merged sequence, split evenly among its
+  // warps; each warp finds both of its bounds in one pass, and the block's
+  // bounds are the first warp's start and the last warp's end
   const long long D = a.M + a.nnzA;
   const long long d0 = (long long)c * D / G, d1 = (long long)(c + 1) * D / G;
-  if (warp == 0) {
-    const long long i0 = merge_path_rows(a.a_rpt, 0, a.M + 1, d0);
-    const long long i1 = merge_path_rows(a.a_rpt, 0, a.M + 1, d1);
-    if (lane == 0) {
-      sm.bc[0] = i0;
-      sm.bc[1] = i1;
-    }
-  }
+  const long long wd0 = d0 + (d1 - d0) * warp / kFlopWarps;
+  const long long wd1 = d0 + (d1 - d0) * (warp + 1) / kFlopWarps;
+  long long wl0, wl1;
+  merge_path_rows2(a.a_rpt, a.M, wd0, wd1, &wl0, &wl1);
+  if (lane == 0 && warp == 0) sm.bc[0] = wl0;
+  if (lane == 0 && warp == kFlopWarps - 1) sm.bc[1] = wl1;
   __syncthreads();
   const long long bi0 = sm.bc[0], bi1 = sm.bc[1];
   const int i0 = (int)bi0, i1 = (int)bi1;
   const int j0 = (int)min(max(d0 - bi0, 0ll), (long long)a.nnzA);
   const int j1 = (int)max(min(max(d1 - bi1, 0ll), (long long)a.nnzA), (long long)j0);
-  const long long wd0 = d0 + (d1 - d0) * warp / kFlopWarps;
-  const long long wd1 = d0 + (d1 - d0) * (warp + 1) / kFlopWarps;
-  const long long wl0 = merge_path_rows(a.a_rpt, bi0, bi1 + 1, wd0);
-  const long long wl1 = merge_path_rows(a.a_rpt, bi0, bi1 + 1, wd1);
   const int wi0 = (int)wl0, wi1 = (int)wl1;
   const int wj0 = (int)min(max(wd0 - wl0, (long long)j0), (long long)j1);
   const int wj1 = (int)min(max(wd1 - wl1, (long long)wj0), (long long)j1);
