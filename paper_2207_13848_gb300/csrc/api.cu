@@ -137,6 +137,9 @@ DedupArgs dedup_args(const spgemm_csr_t* A, const spgemm_csr_t* B, const Workspa
   d.n_cand = A->rows;
   d.nnz_out = nullptr;
   d.ws = w;
+  d.heavy_cap = A->rows;
+  d.heavy_case = nullptr;
+  d.case_id = 0;
   return d;
 }
 

@@ -39,6 +39,11 @@ struct DedupArgs {
   int64_t n_cand;      // candidates: M (Bernoulli, all rows) or the number of draws
   int* nnz_out;        // all-rows mode: nnz per row (int32[M]); otherwise null
   Workspace ws;
+  // heavy-row queue: ws.heavy (capacity heavy_cap), plus the case id of each
+  // entry in heavy_case when several predictions share the queue (else null)
+  long long heavy_cap;
+  int* heavy_case;
+  int case_id;
 };
 
 __device__ __forceinline__ uint32_t mix_key(int key) { return (uint32_t)key * 0x9E3779B1u; }
@@ -172,8 +177,11 @@ __device__ long long dedup_row_warp(const DedupArgs& a, int row, int* tbl, long 
   }
 
   if (lane == 0) {
-    unsigned h = atomicAdd(&a.ws.hdr->heavy_count, 1u);
-    if (h < (unsigned long long)a.M) a.ws.heavy[h] = row;
+    const unsigned h = atomicAdd(&a.ws.hdr->heavy_count, 1u);
+    if (h < (unsigned long long)a.heavy_cap) {
+      a.ws.heavy[h] = row;
+      if (a.heavy_case) a.heavy_case[h] = a.case_id;
+    }
   }
   return -1;
 }
@@ -309,39 +317,48 @@ __device__ long long heavy_count_pass(const DedupArgs& a, long long rb, long lon
   return block_sum<kHeavyThreads>(cnt, sm.red);
 }
 
+// Exact nnz of one heavy row by the whole block (kHeavyThreads threads): a
+// shared hash table when the row has at most kBlockHashCap products, else a
+// bitmap over B's columns, one column range of bitmap_words * 32 at a time.
+__device__ long long heavy_row_nnz(const DedupArgs& a, int row, HeavySmem& sm, unsigned* tab,
+                                   int bitmap_words, bool& bad) {
+  long long rb = __ldg(a.a_rpt + row), re = __ldg(a.a_rpt + row + 1);
+  if (!clamp_range(rb, re, a.nnzA)) bad = true;
+  // the row's FLOP decides the method
+  long long fl = 0;
+  for (long long j = rb + threadIdx.x; j < re; j += kHeavyThreads) {
+    long long s, len;
+    b_row(a, __ldg(a.a_col + j), s, len, bad);
+    fl += len;
+  }
+  const long long flop = block_sum<kHeavyThreads>(fl, sm.red);
+  long long nnz = 0;
+  if (flop <= kBlockHashCap) {
+    const int lg = ceil_log2((uint32_t)(2 * flop));
+    for (int i = threadIdx.x; i < (1 << lg); i += kHeavyThreads) tab[i] = 0xffffffffu;
+    __syncthreads();
+    nnz = heavy_count_pass<false>(a, rb, re, sm, tab, lg, 0, 0, bad);
+  } else {
+    const long long range = (long long)bitmap_words * 32;
+    for (long long lo = 0; lo < a.N; lo += range) {
+      const long long hi = min((long long)a.N, lo + range);
+      const int words = (int)((hi - lo + 31) / 32);
+      for (int i = threadIdx.x; i < words; i += kHeavyThreads) tab[i] = 0u;
+      __syncthreads();
+      nnz += heavy_count_pass<true>(a, rb, re, sm, tab, words, lo, hi, bad);
+    }
+  }
+  return nnz;
+}
+
 __global__ void __launch_bounds__(kHeavyThreads) k_dedup_heavy(DedupArgs a, int bitmap_words) {
   extern __shared__ unsigned tab[];
   __shared__ HeavySmem sm;
-  const unsigned n_heavy = min(a.ws.hdr->heavy_count, (unsigned)a.M);
+  const unsigned n_heavy = (unsigned)min((long long)a.ws.hdr->heavy_count, a.heavy_cap);
   for (unsigned h = blockIdx.x; h < n_heavy; h += gridDim.x) {
     const int row = a.ws.heavy[h];
     bool bad = false;
-    long long rb = __ldg(a.a_rpt + row), re = __ldg(a.a_rpt + row + 1);
-    if (!clamp_range(rb, re, a.nnzA)) bad = true;
-    // the row's FLOP decides the method
-    long long fl = 0;
-    for (long long j = rb + threadIdx.x; j < re; j += kHeavyThreads) {
-      long long s, len;
-      b_row(a, __ldg(a.a_col + j), s, len, bad);
-      fl += len;
-    }
-    const long long flop = block_sum<kHeavyThreads>(fl, sm.red);
-    long long nnz = 0;
-    if (flop <= kBlockHashCap) {
-      const int lg = ceil_log2((uint32_t)(2 * flop));
-      for (int i = threadIdx.x; i < (1 << lg); i += kHeavyThreads) tab[i] = 0xffffffffu;
-      __syncthreads();
-      nnz = heavy_count_pass<false>(a, rb, re, sm, tab, lg, 0, 0, bad);
-    } else {
-      const long long range = (long long)bitmap_words * 32;
-      for (long long lo = 0; lo < a.N; lo += range) {
-        const long long hi = min((long long)a.N, lo + range);
-        const int words = (int)((hi - lo + 31) / 32);
-        for (int i = threadIdx.x; i < words; i += kHeavyThreads) tab[i] = 0u;
-        __syncthreads();
-        nnz += heavy_count_pass<true>(a, rb, re, sm, tab, words, lo, hi, bad);
-      }
-    }
+    const long long nnz = heavy_row_nnz(a, row, sm, tab, bitmap_words, bad);
     if (threadIdx.x == 0) {
       atomicAdd(&a.ws.hdr->z_acc, (unsigned long long)nnz);
       if (a.nnz_out) a.nnz_out[row] = (int)nnz;

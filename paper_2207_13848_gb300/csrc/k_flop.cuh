@@ -103,31 +103,41 @@ struct WarpInfo {
   int pad[3];
 };
 
+// What a block's pass over one range of the merged sequence leaves behind.
+struct RangeOut {
+  int i0, i1, j0;              // rows [i0, i1) end in the range; j0 = its first nonzero
+  long long run;               // partial FLOP of the row open at the range's end
+  long long head_known;        // the first row's FLOP minus the carry (if head_pending)
+  long long extra_f, extra_p;  // FLOP / predictions of rows split between warps
+  bool dep;                    // the whole range lies inside one row
+  bool head_pending;           // the first row waits for the previous range's carry
+};
+
 struct FlopShared {
   alignas(16) int lens[kFlopWarps][kSub];  // prefix sums of B row lengths over a warp's step
   WarpInfo info[kFlopWarps];
   long long red[kFlopWarps + 1];
   long long bc[8];
+  RangeOut out;
 };
 
+// One block streams the items [d0, d1) of the merged sequence: every row that
+// ends in the range and starts in it gets its prediction (predict mode) or its
+// FLOP written; rows split between warps are joined here; the row split with
+// the previous range (has_prev) and the row left open at the end are reported
+// in *out (written by thread 0; all threads may read it on return).  ftot/ptot
+// receive this thread's share of the FLOP / prediction sums of finished rows.
 template <int MODE>
-__global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) k_flop_pred(FlopArgs a) {
-  __shared__ FlopShared sm;
+__device__ __forceinline__ void flop_range(const FlopArgs& a, long long d0, long long d1, bool has_prev,
+                                           unsigned long long fz, unsigned long long zz, double ratio,
+                                           FlopShared& sm, RangeOut* out, long long& ftot,
+                                           long long& ptot, bool& bad) {
+  // ---- the range is split evenly among the block's warps; each warp finds
+  // both of its bounds in one pass, and the range's bounds are the first
+  // warp's start and the last warp's end
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int G = gridDim.x, c = blockIdx.x;
-  WsHeader* hdr = a.ws.hdr;
-  const unsigned ep = *reinterpret_cast<volatile unsigned*>(&hdr->epoch) + 1u;
-  Slot* slots = a.ws.slots;
   const int K = (int)a.K;
   const int M = (int)a.M;
-  const unsigned long long fz = hdr->f_acc, zz = hdr->z_acc;
-  const double ratio = (MODE == kModePredict && fz) ? (double)zz / (double)fz : 0.0;
-
-  // ---- this block's share of the merged sequence, split evenly among its
-  // warps; each warp finds both of its bounds in one pass, and the block's
-  // bounds are the first warp's start and the last warp's end
-  const long long D = a.M + a.nnzA;
-  const long long d0 = (long long)c * D / G, d1 = (long long)(c + 1) * D / G;
   const long long wd0 = d0 + (d1 - d0) * warp / kFlopWarps;
   const long long wd1 = d0 + (d1 - d0) * (warp + 1) / kFlopWarps;
   long long wl0, wl1;
@@ -146,8 +156,6 @@ __global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) k_flop_pred
   const int rows_hi = wtail ? wi1 + 1 : wi1;  // rows touched: [wi0, rows_hi)
   const bool whead = wi0 < M && __ldg(a.a_rpt + wi0) < wj0;  // first row started earlier
 
-  bool bad = false;
-  long long ftot = 0, ptot = 0;  // per-lane sums over rows this warp completes
   int head_part = 0, tail_part = 0;
   int* lw = sm.lens[warp];
 
@@ -302,11 +310,11 @@ __global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) k_flop_pred
     w.head_part = head_part;
     w.tail_part = tail_part;
   }
-  const bool blk_head_split = (i0 < M) && (c > 0) && (__ldg(a.a_rpt + i0) < j0);
-  if (__syncthreads_or(bad) && t == 0) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
+  const bool blk_head_split = (i0 < M) && has_prev && (__ldg(a.a_rpt + i0) < j0);
+  __syncthreads();
 
-  // ---- rows split between warps (thread 0).  Only the block's first row can
-  // depend on the carry from the previous block.
+  // ---- rows split between warps (thread 0).  Only the range's first row can
+  // depend on the carry from the previous range.
   if (t == 0) {
     long long run = 0;          // partial of the open row entering warp w
     bool dep = blk_head_split;  // ... plus the previous block's carry
@@ -339,6 +347,44 @@ __global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) k_flop_pred
       dep = false;
       run = in.tail_part;
     }
+    out->i0 = i0;
+    out->i1 = i1;
+    out->j0 = j0;
+    out->run = run;
+    out->head_known = head_known;
+    out->extra_f = extra_f;
+    out->extra_p = extra_p;
+    out->dep = dep;
+    out->head_pending = head_pending;
+  }
+  __syncthreads();
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) k_flop_pred(FlopArgs a) {
+  __shared__ FlopShared sm;
+  const int t = threadIdx.x;
+  const int G = gridDim.x, c = blockIdx.x;
+  WsHeader* hdr = a.ws.hdr;
+  const unsigned ep = *reinterpret_cast<volatile unsigned*>(&hdr->epoch) + 1u;
+  Slot* slots = a.ws.slots;
+  const int M = (int)a.M;
+  const unsigned long long fz = hdr->f_acc, zz = hdr->z_acc;
+  const double ratio = (MODE == kModePredict && fz) ? (double)zz / (double)fz : 0.0;
+
+  // ---- this block's share of the merged sequence
+  const long long D = a.M + a.nnzA;
+  const long long d0 = (long long)c * D / G, d1 = (long long)(c + 1) * D / G;
+  bool bad = false;
+  long long ftot = 0, ptot = 0;
+  flop_range<MODE>(a, d0, d1, c > 0, fz, zz, ratio, sm, &sm.out, ftot, ptot, bad);
+  if (__syncthreads_or(bad) && t == 0) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
+  const int i0 = sm.out.i0, i1 = sm.out.i1;
+
+  if (t == 0) {
+    const long long run = sm.out.run, head_known = sm.out.head_known;
+    const bool dep = sm.out.dep, head_pending = sm.out.head_pending;
+    long long extra_f = sm.out.extra_f, extra_p = sm.out.extra_p;
     // carries between blocks (waits only on block c-1)
     if (dep) {
       // the whole block lies inside one row: pass the carry on
