@@ -210,6 +210,109 @@ int spgemm_predict_structure_static(const spgemm_csr_t* A, const spgemm_csr_t* B
                                     int64_t* offsets, int32_t* flop_row, spgemm_result_t* res,
                                     void* stream);
 
+/* ---- batched prediction ---------------------------------------------------------------
+ * Many independent predictions ("cases") of uneven sizes computed together: the
+ * paper's method (Eq. 4, Algorithm 2) for every case, exactly as
+ * spgemm_predict_structure computes it, but as one set of four persistent
+ * launches that span the whole batch, so small cases share the GPU instead of
+ * each paying the latency of its own launches.  The paper predicts one product
+ * at a time; batching is a library feature for callers with many products.
+ * Per case, every output (pred_row, offsets, flop_row, the result record) is
+ * bit-identical to spgemm_predict_structure with the same arguments, whatever
+ * the batch composition and the tuning.
+ *
+ * Use: spgemm_batch_workspace_size -> allocate and zero-fill the workspace ->
+ * spgemm_batch_prepare (writes the plan into the workspace) ->
+ * spgemm_predict_batch as often as wanted (inputs may change between runs, their
+ * shapes and addresses may not; graph-capturable).  A new batch needs a new
+ * spgemm_batch_prepare on the same workspace. */
+
+/* One case: operands, sampling configuration and outputs, with the meaning and
+ * layout of spgemm_predict_structure's arguments (device memory, caller-owned).
+ * cfg.mode is SPGEMM_SAMPLE_BERNOULLI or SPGEMM_SAMPLE_PAPER_DRAW. */
+typedef struct spgemm_batch_item {
+  spgemm_csr_t A;
+  spgemm_csr_t B;
+  spgemm_config_t cfg;
+  int32_t* pred_row;        /* int32[A.rows] */
+  int64_t* offsets;         /* int64[A.rows + 1] */
+  int32_t* flop_row;        /* int32[A.rows], or NULL */
+  spgemm_result_t* res;     /* one record per case */
+} spgemm_batch_item_t;
+
+/* Launch parameters of the batch; they change speed, never results.  0 selects
+ * the default.  spgemm_batch_autotune measures candidates and picks one. */
+typedef struct spgemm_batch_tuning {
+  int32_t tile_items;         /* rows + nonzeros of A per FLOP tile, in [4096, 2^24]; default 16384 */
+  int32_t warp_table;         /* hash slots per warp of the sampled-row pass: 512, 1024 or 2048;
+                                 default 1024 */
+  int32_t heavy_threshold;    /* products of a sampled row above which it is counted by a whole
+                                 thread block instead of a warp, in [32, warp_table / 2];
+                                 default warp_table / 2 */
+  int32_t sample_chunk;       /* candidates per unit of work of the sampled-row pass, a
+                                 multiple of 256 in [4096, 2^24]; default 32768 */
+  int32_t flop_blocks_per_sm; /* resident blocks per SM of the FLOP pass, 1 .. what fits;
+                                 default what fits */
+  int32_t reserved[3];        /* must be 0 */
+} spgemm_batch_tuning_t;
+
+/* What spgemm_batch_prepare planned; pass it to spgemm_predict_batch. */
+typedef struct spgemm_batch_plan {
+  int32_t n_cases;
+  int32_t reserved0;
+  int64_t total_rows;         /* sum of A.rows */
+  int64_t total_candidates;   /* sum of the sample candidates (rows or draws) */
+  int64_t total_tiles;        /* FLOP tiles */
+  int64_t total_chunks;       /* work units of the sampled-row pass */
+  int64_t total_table_blocks; /* blocks of the B row-length table pass */
+  uint64_t ws_bytes;          /* workspace bytes the plan uses */
+  spgemm_batch_tuning_t tuning; /* the tuning in force, defaults filled in */
+} spgemm_batch_plan_t;
+
+#define SPGEMM_BATCH_MAX_CASES (1 << 20)
+
+/* Device workspace bytes for this batch under any tuning (0 for invalid
+ * arguments).  About 4 bytes per row and 1 byte per column of A, 64 bytes
+ * per 4096 rows + nonzeros of A, and 450 bytes per case. */
+size_t spgemm_batch_workspace_size(const spgemm_batch_item_t* items, int32_t n);
+
+/* Host bytes of the staging buffer spgemm_batch_prepare copies the plan from,
+ * under any tuning. */
+size_t spgemm_batch_staging_size(const spgemm_batch_item_t* items, int32_t n);
+
+/* Checks every case as spgemm_predict_structure would (on the first failure,
+ * returns its code and writes the case index to *bad_item when bad_item is not
+ * NULL; nothing is queued), plans the batch under `tuning` (NULL = defaults)
+ * into *plan, and queues on `stream` the copy of the plan into the workspace.
+ * host_staging: page-locked host memory of at least spgemm_batch_staging_size
+ * bytes that must stay untouched until the copy has completed on `stream`; or
+ * NULL, in which case the call builds the plan in its own host memory and
+ * returns only once the copy has completed.  The workspace must have been
+ * zero-filled once before its first use; spgemm_batch_prepare may be called on
+ * it again for another batch. */
+int spgemm_batch_prepare(const spgemm_batch_item_t* items, int32_t n,
+                         const spgemm_batch_tuning_t* tuning, spgemm_batch_plan_t* plan,
+                         void* ws, size_t ws_bytes, void* host_staging, size_t staging_bytes,
+                         int32_t* bad_item, void* stream);
+
+/* Runs the prepared batch on `stream`: four kernel launches and one 64-byte
+ * memset, no host synchronisation, capturable in a CUDA graph.  Every case's
+ * outputs and result record are written as by spgemm_predict_structure;
+ * result status bits are per case. */
+int spgemm_predict_batch(const spgemm_batch_plan_t* plan, void* ws, size_t ws_bytes, void* stream);
+
+/* Picks a tuning for this batch by measurement: prepares and runs the batch
+ * under each candidate (hash-table size and heavy-row threshold, chunk size,
+ * tile size, blocks per SM), `reps` timed runs each after one untimed run, and
+ * writes the fastest (by the median of the runs) to *best and its time in
+ * milliseconds to *best_ms (when not NULL).  Synchronous: blocks the host until
+ * the measurements are done.  Leaves the workspace prepared with *best (as
+ * spgemm_batch_prepare with *best and no staging buffer would) and the plan in
+ * *plan.  Outputs are overwritten with the batch's (identical) results. */
+int spgemm_batch_autotune(const spgemm_batch_item_t* items, int32_t n, void* ws, size_t ws_bytes,
+                          int32_t reps, spgemm_batch_tuning_t* best, float* best_ms,
+                          spgemm_batch_plan_t* plan, void* stream);
+
 /* Static description of a host return code or of a status bit set. */
 const char* spgemm_status_string(int code);
 

@@ -50,6 +50,39 @@ class ConfigStruct(ctypes.Structure):
 
 
 RESULT_BYTES = 48  # spgemm_result_t: 5 x int64 + 2 x int32
+BATCH_MAX_CASES = 1 << 20
+
+
+class BatchItemStruct(ctypes.Structure):
+    _fields_ = [("A", CsrStruct), ("B", CsrStruct), ("cfg", ConfigStruct),
+                ("pred_row", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("flop_row", ctypes.c_void_p), ("res", ctypes.c_void_p)]
+
+
+class TuningStruct(ctypes.Structure):
+    _fields_ = [("tile_items", ctypes.c_int32), ("warp_table", ctypes.c_int32),
+                ("heavy_threshold", ctypes.c_int32), ("sample_chunk", ctypes.c_int32),
+                ("flop_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k in ("tile_items", "warp_table", "heavy_threshold",
+                                               "sample_chunk", "flop_blocks_per_sm")}
+
+
+class PlanStruct(ctypes.Structure):
+    _fields_ = [("n_cases", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("total_rows", ctypes.c_int64), ("total_candidates", ctypes.c_int64),
+                ("total_tiles", ctypes.c_int64), ("total_chunks", ctypes.c_int64),
+                ("total_table_blocks", ctypes.c_int64), ("ws_bytes", ctypes.c_uint64),
+                ("tuning", TuningStruct)]
+
+
+def tuning(**kw):
+    """A TuningStruct; unnamed fields are 0 (the library's defaults)."""
+    t = TuningStruct()
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    return t
 
 _lib = None
 
@@ -85,6 +118,19 @@ def load():
     lib.spgemm_predict_structure_static.restype = ctypes.c_int
     lib.spgemm_set_profile_events.argtypes = [P, P]
     lib.spgemm_set_profile_events.restype = ctypes.c_int
+    I = ctypes.POINTER(BatchItemStruct)
+    T = ctypes.POINTER(TuningStruct)
+    PL = ctypes.POINTER(PlanStruct)
+    i32 = ctypes.c_int32
+    lib.spgemm_batch_workspace_size.restype = sz
+    lib.spgemm_batch_workspace_size.argtypes = [I, i32]
+    lib.spgemm_batch_staging_size.restype = sz
+    lib.spgemm_batch_staging_size.argtypes = [I, i32]
+    lib.spgemm_batch_prepare.argtypes = [I, i32, T, PL, P, sz, P, sz, ctypes.POINTER(i32), P]
+    lib.spgemm_predict_batch.argtypes = [PL, P, sz, P]
+    lib.spgemm_batch_autotune.argtypes = [I, i32, P, sz, i32, T, ctypes.POINTER(ctypes.c_float), PL, P]
+    for fn in (lib.spgemm_batch_prepare, lib.spgemm_predict_batch, lib.spgemm_batch_autotune):
+        fn.restype = ctypes.c_int
     lib.spgemm_status_string.restype = ctypes.c_char_p
     lib.spgemm_status_string.argtypes = [ctypes.c_int]
     for fn in (lib.spgemm_flop_per_row, lib.spgemm_predict_cr, lib.spgemm_predict_structure,
@@ -254,6 +300,37 @@ def spgemm_status_string(code):
     return load().spgemm_status_string(int(code)).decode()
 
 
+def spgemm_batch_workspace_size(items, n):
+    return int(load().spgemm_batch_workspace_size(items, int(n)))
+
+
+def spgemm_batch_staging_size(items, n):
+    return int(load().spgemm_batch_staging_size(items, int(n)))
+
+
+def spgemm_batch_prepare(items, n, tuning_, plan, ws, host_staging, bad_item, stream=None):
+    """items: ctypes array of BatchItemStruct; tuning_: TuningStruct or None;
+    plan: PlanStruct (written); host_staging: pinned torch CPU tensor or None;
+    bad_item: ctypes.c_int32 or None."""
+    hs = None if host_staging is None else ctypes.c_void_p(host_staging.data_ptr())
+    hb = 0 if host_staging is None else host_staging.numel() * host_staging.element_size()
+    return load().spgemm_batch_prepare(items, int(n), ctypes.byref(tuning_) if tuning_ is not None else None,
+                                       ctypes.byref(plan), ws.ptr(), ws.nbytes, hs, hb,
+                                       ctypes.byref(bad_item) if bad_item is not None else None,
+                                       _stream(stream))
+
+
+def spgemm_predict_batch(plan, ws, stream=None):
+    return load().spgemm_predict_batch(ctypes.byref(plan), ws.ptr(), ws.nbytes, _stream(stream))
+
+
+def spgemm_batch_autotune(items, n, ws, reps, best, best_ms, plan, stream=None):
+    """best: TuningStruct (written); best_ms: ctypes.c_float or None; plan: PlanStruct (written)."""
+    return load().spgemm_batch_autotune(items, int(n), ws.ptr(), ws.nbytes, int(reps), ctypes.byref(best),
+                                        ctypes.byref(best_ms) if best_ms is not None else None,
+                                        ctypes.byref(plan), _stream(stream))
+
+
 # ---- convenience wrappers -------------------------------------------------------
 @dataclass
 class Prediction:
@@ -342,3 +419,63 @@ def predict_structure_host(A_host, B_host, cfg, ws=None, device="cuda", stream=N
     res = p.res.to("cpu", non_blocking=True)
     torch.cuda.current_stream().synchronize()
     return pred.numpy(), offsets.numpy(), read_result(res)
+
+
+class Batch:
+    """Many predictions in one batched run (spgemm_predict_batch).
+
+    ``cases`` is a list of (A, B, cfg) with DeviceCSR operands.  Outputs are
+    allocated per case (pred, offsets, optional flop) and the result records of
+    all cases share one int64 tensor [n, 6], so one copy reads them all."""
+
+    def __init__(self, cases, want_flop=False, device="cuda", tuning_=None, pinned=True):
+        torch = _torch()
+        self.cases = list(cases)
+        self.n = len(self.cases)
+        self.device = device
+        self.res = torch.zeros((self.n, RESULT_BYTES // 8), dtype=torch.int64, device=device)
+        self.outputs = [_outputs(A.rows, device, want_flop) for A, _, _ in self.cases]
+        self.items = (BatchItemStruct * self.n)()
+        for i, ((A, B, cfg), (pred, offs, flop)) in enumerate(zip(self.cases, self.outputs)):
+            it = self.items[i]
+            it.A, it.B, it.cfg = A.struct(), B.struct(), cfg
+            it.pred_row = pred.data_ptr() if A.rows > 0 else None
+            it.offsets = offs.data_ptr()
+            it.flop_row = flop.data_ptr() if (flop is not None and A.rows > 0) else None
+            it.res = self.res[i].data_ptr()
+        nbytes = spgemm_batch_workspace_size(self.items, self.n)
+        if nbytes == 0:
+            raise RuntimeError("spgemm_batch_workspace_size rejected the batch")
+        self.ws = Workspace(nbytes, device)
+        sbytes = spgemm_batch_staging_size(self.items, self.n)
+        self.staging = torch.empty(sbytes, dtype=torch.uint8, pin_memory=pinned) if sbytes else None
+        self.plan = PlanStruct()
+        self.prepare(tuning_)
+
+    def prepare(self, tuning_=None, stream=None):
+        bad = ctypes.c_int32(-1)
+        rc = spgemm_batch_prepare(self.items, self.n, tuning_, self.plan, self.ws, self.staging, bad, stream)
+        if rc != OK:
+            raise RuntimeError(f"spgemm_batch_prepare failed on case {bad.value}: "
+                               f"{spgemm_status_string(rc)} ({rc})")
+        return self.plan
+
+    def run(self, stream=None):
+        _check(spgemm_predict_batch(self.plan, self.ws, stream), "spgemm_predict_batch")
+
+    def autotune(self, reps=3, stream=None):
+        best, ms = TuningStruct(), ctypes.c_float(0)
+        _check(spgemm_batch_autotune(self.items, self.n, self.ws, reps, best, ms, self.plan, stream),
+               "spgemm_batch_autotune")
+        return best, ms.value
+
+    def results(self):
+        """Host list of result dicts, one per case."""
+        rows = self.res.cpu().tolist()
+        return [dict(flop_total=v[0], flop_s=v[1], nnz_s=v[2], n_sampled=v[3], pred_total=v[4],
+                     status=v[5] & 0xFFFFFFFF) for v in rows]
+
+    def prediction(self, i):
+        pred, offs, flop = self.outputs[i]
+        return Prediction(pred, offs, flop, self.res[i])
+

@@ -1,16 +1,26 @@
 // C ABI of the structure predictor: argument checks on the host, then the
 // launches of each entry point on the caller's stream.  No allocation, no
 // synchronisation.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
+#include "k_batch.cuh"
 #include "k_dedup.cuh"
 #include "k_flop.cuh"
 #include "k_scan.cuh"
 
 using namespace spg;
+
+static_assert(sizeof(spgemm_csr_t) == 40, "spgemm_csr_t layout");
+static_assert(sizeof(spgemm_config_t) == 32, "spgemm_config_t layout");
+static_assert(sizeof(spgemm_result_t) == 48, "spgemm_result_t layout");
+static_assert(sizeof(spgemm_batch_item_t) == 144, "spgemm_batch_item_t layout");
+static_assert(sizeof(spgemm_batch_tuning_t) == 32, "spgemm_batch_tuning_t layout");
+static_assert(sizeof(spgemm_batch_plan_t) == 88, "spgemm_batch_plan_t layout");
 
 namespace {
 
@@ -25,6 +35,11 @@ struct DeviceLimits {
   int dedup_blocks_per_sm = 0;
   int heavy_dyn_smem = 0;
   int heavy_bitmap_words = 0;
+  // batched prediction
+  int kb_sample_blocks_per_sm[3] = {0, 0, 0};  // warp tables of 512, 1024, 2048 slots
+  int kb_flop_blocks_per_sm = 0;
+  int kb_heavy_dyn_smem = 0;
+  int kb_heavy_bitmap_words = 0;
   bool ok = false;
 };
 
@@ -67,7 +82,27 @@ void init_limits(int dev, DeviceLimits* L) {
   L->scan_blocks_per_sm = min(b, b2);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dedup_rows, kDedupThreads, dedup_dyn_smem()) != cudaSuccess) return;
   L->dedup_blocks_per_sm = b;
-  L->ok = L->flop_blocks_per_sm > 0 && L->scan_blocks_per_sm > 0 && L->dedup_blocks_per_sm > 0;
+  // batched prediction
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kb_heavy) != cudaSuccess) return;
+  int kdyn = (int)p.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes - 1024;
+  kdyn = (kdyn / 4096) * 4096;
+  if (kdyn < kBlockHashSlots * 4) return;
+  if (cudaFuncSetAttribute(kb_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, kdyn) != cudaSuccess) return;
+  L->kb_heavy_dyn_smem = kdyn;
+  L->kb_heavy_bitmap_words = kdyn / 4;
+  const void* samplers[3] = {(const void*)kb_sample<512>, (const void*)kb_sample<1024>, (const void*)kb_sample<2048>};
+  for (int i = 0; i < 3; ++i) {
+    const int sm = kDedupWarps * (512 << i) * (int)sizeof(int);
+    if (cudaFuncSetAttribute(samplers[i], cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess) return;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, samplers[i], kDedupThreads, sm) != cudaSuccess) return;
+    L->kb_sample_blocks_per_sm[i] = b;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kb_flop, kFlopThreads, 0) != cudaSuccess) return;
+  L->kb_flop_blocks_per_sm = b;
+  L->ok = L->flop_blocks_per_sm > 0 && L->scan_blocks_per_sm > 0 && L->dedup_blocks_per_sm > 0 &&
+          L->kb_flop_blocks_per_sm > 0 && L->kb_sample_blocks_per_sm[0] > 0 &&
+          L->kb_sample_blocks_per_sm[1] > 0 && L->kb_sample_blocks_per_sm[2] > 0;
 }
 
 const DeviceLimits* limits() {
@@ -137,9 +172,12 @@ DedupArgs dedup_args(const spgemm_csr_t* A, const spgemm_csr_t* B, const Workspa
   d.n_cand = A->rows;
   d.nnz_out = nullptr;
   d.ws = w;
+  d.status = &w.hdr->status;
+  d.heavy_count = &w.hdr->heavy_count;
+  d.heavy = w.heavy;
   d.heavy_cap = A->rows;
-  d.heavy_case = nullptr;
-  d.case_id = 0;
+  d.heavy_base = 0;
+  d.heavy_thr = kWarpCap;
   return d;
 }
 
@@ -247,6 +285,267 @@ void init_static_scratch(int dev) {
   void* p = nullptr;
   g_static_err[dev] = cudaGetSymbolAddress(&p, g_static_scratch);
   g_static_ptr[dev] = g_static_err[dev] == cudaSuccess ? p : nullptr;
+}
+
+// ---- batched prediction ---------------------------------------------------------
+constexpr int kDefTile = 16384, kMinTile = 4096, kMaxTile = 1 << 24;
+constexpr int kDefChunk = 32768, kMinChunk = 4096, kMaxChunk = 1 << 24;
+constexpr int kDefTable = 1024;
+
+size_t r256(size_t b) { return (b + 255) / 256 * 256; }
+size_t r16(size_t b) { return (b + 15) / 16 * 16; }
+
+// Regions of the batch workspace, in order.  [cases, slots) is the plan copied
+// from the host; the deg8 tables follow the heavy-row queue.
+struct BatchLayout {
+  size_t hdr, acc, cases, tile_case, chunk_case, tab_case, slots, heavy, deg, total;
+  size_t plan_bytes() const { return slots - cases; }
+};
+
+BatchLayout batch_layout(long long n, long long tiles, long long chunks, long long tab_blocks,
+                         long long heavy_cap, long long deg_bytes) {
+  BatchLayout l;
+  size_t p = 0;
+  l.hdr = p;
+  p += r256(sizeof(BatchHeader));
+  l.acc = p;
+  p += r256(sizeof(CaseAcc) * (size_t)n);
+  l.cases = p;
+  p += r256(sizeof(BatchCase) * (size_t)n);
+  l.tile_case = p;
+  p += r256(4 * (size_t)tiles);
+  l.chunk_case = p;
+  p += r256(4 * (size_t)(chunks > 0 ? chunks : 1));
+  l.tab_case = p;
+  p += r256(4 * (size_t)(tab_blocks > 0 ? tab_blocks : 1));
+  l.slots = p;
+  p += sizeof(Slot) * (size_t)tiles;
+  l.heavy = p;
+  p += r256(4 * (size_t)(heavy_cap > 0 ? heavy_cap : 1));
+  l.deg = p;
+  p += r256((size_t)deg_bytes);
+  l.total = p;
+  return l;
+}
+
+int resolve_tuning(const spgemm_batch_tuning_t* in, const DeviceLimits* L, spgemm_batch_tuning_t* out) {
+  spgemm_batch_tuning_t t{};
+  if (in) t = *in;
+  if (t.reserved[0] || t.reserved[1] || t.reserved[2]) return SPGEMM_ERR_INVALID_ARG;
+  if (t.tile_items == 0) t.tile_items = kDefTile;
+  if (t.warp_table == 0) t.warp_table = kDefTable;
+  if (t.heavy_threshold == 0) t.heavy_threshold = t.warp_table / 2;
+  if (t.sample_chunk == 0) t.sample_chunk = kDefChunk;
+  if (t.flop_blocks_per_sm == 0 && L) t.flop_blocks_per_sm = L->kb_flop_blocks_per_sm;
+  if (t.tile_items < kMinTile || t.tile_items > kMaxTile) return SPGEMM_ERR_INVALID_ARG;
+  if (t.warp_table != 512 && t.warp_table != 1024 && t.warp_table != 2048) return SPGEMM_ERR_INVALID_ARG;
+  if (t.heavy_threshold < 32 || t.heavy_threshold > t.warp_table / 2) return SPGEMM_ERR_INVALID_ARG;
+  if (t.sample_chunk < kMinChunk || t.sample_chunk > kMaxChunk || t.sample_chunk % 256) return SPGEMM_ERR_INVALID_ARG;
+  if (t.flop_blocks_per_sm < 0 || (L && (t.flop_blocks_per_sm < 1 || t.flop_blocks_per_sm > L->kb_flop_blocks_per_sm)))
+    return SPGEMM_ERR_INVALID_ARG;
+  *out = t;
+  return SPGEMM_OK;
+}
+
+// Host checks of one case, as spgemm_predict_structure makes them.
+int check_item(const spgemm_batch_item_t& it, long long* n_cand) {
+  const spgemm_csr_t* A = &it.A;
+  const spgemm_csr_t* B = &it.B;
+  if (!csr_ok(A) || !csr_ok(B) || !it.res) return SPGEMM_ERR_INVALID_ARG;
+  if (A->cols != B->rows) return SPGEMM_ERR_DIM_MISMATCH;
+  if (!csr_fits(A) || !csr_fits(B)) return SPGEMM_ERR_TOO_LARGE;
+  if (!it.offsets || (!it.pred_row && A->rows > 0)) return SPGEMM_ERR_INVALID_ARG;
+  return sample_candidates(&it.cfg, A->rows, n_cand);
+}
+
+long long tiles_of(const spgemm_batch_item_t& it, long long tile) {
+  const long long D = it.A.rows + it.A.nnz;
+  const long long t = (D + tile - 1) / tile;
+  return t > 0 ? t : 1;
+}
+long long tab_blocks_of(const spgemm_batch_item_t& it) {
+  return (it.A.cols + kTabRowsPerBlock - 1) / kTabRowsPerBlock;
+}
+
+// Totals of a batch under tile size `tile` and chunk size `chunk`; returns the
+// first failing case's code (and index) or SPGEMM_OK.
+struct BatchTotals {
+  long long rows = 0, cand = 0, tiles = 0, chunks = 0, tab = 0, deg = 0;
+};
+int batch_totals(const spgemm_batch_item_t* items, int n, long long tile, long long chunk, BatchTotals* T,
+                 int* bad) {
+  BatchTotals t;
+  for (int i = 0; i < n; ++i) {
+    long long nc = 0;
+    const int rc = check_item(items[i], &nc);
+    if (rc) {
+      *bad = i;
+      return rc;
+    }
+    t.rows += items[i].A.rows;
+    t.cand += nc;
+    t.tiles += tiles_of(items[i], tile);
+    t.tab += tab_blocks_of(items[i]);
+    t.deg += (long long)r16((size_t)items[i].A.cols + 16);
+  }
+  t.chunks = (t.cand + chunk - 1) / chunk;
+  if (t.rows >= kIdxMax || t.tiles >= kIdxMax || t.tab >= kIdxMax) return SPGEMM_ERR_TOO_LARGE;
+  *T = t;
+  return SPGEMM_OK;
+}
+
+BatchLayout layout_of(const BatchTotals& t, int n) {
+  return batch_layout(n, t.tiles, t.chunks, t.tab, t.cand, t.deg);
+}
+
+BatchArgs batch_args(const spgemm_batch_plan_t* plan, void* ws) {
+  const BatchLayout l = batch_layout(plan->n_cases, plan->total_tiles, plan->total_chunks,
+                                     plan->total_table_blocks, plan->total_candidates, 0);
+  char* base = static_cast<char*>(ws);
+  BatchArgs b;
+  b.hdr = reinterpret_cast<BatchHeader*>(base + l.hdr);
+  b.cases = reinterpret_cast<const BatchCase*>(base + l.cases);
+  b.acc = reinterpret_cast<CaseAcc*>(base + l.acc);
+  b.slots = reinterpret_cast<Slot*>(base + l.slots);
+  b.tile_case = reinterpret_cast<const int*>(base + l.tile_case);
+  b.chunk_case = reinterpret_cast<const int*>(base + l.chunk_case);
+  b.tab_case = reinterpret_cast<const int*>(base + l.tab_case);
+  b.heavy = reinterpret_cast<int*>(base + l.heavy);
+  b.n_cases = plan->n_cases;
+  b.total_tiles = (int)plan->total_tiles;
+  b.total_cand = plan->total_candidates;
+  b.total_chunks = plan->total_chunks;
+  b.sample_chunk = plan->tuning.sample_chunk;
+  b.heavy_cap = plan->total_candidates;
+  b.heavy_thr = plan->tuning.heavy_threshold;
+  return b;
+}
+
+// Queues the batch: counters reset, then the four launches.  ev (optional,
+// 5 events) is recorded before the first launch and after each phase: tables,
+// sampled rows, heavy rows, FLOP.
+int launch_batch(const DeviceLimits* L, const spgemm_batch_plan_t* plan, void* ws, cudaStream_t st,
+                 cudaEvent_t* ev) {
+  const BatchArgs b = batch_args(plan, ws);
+  if (cudaMemsetAsync(b.hdr, 0, kBatchCounterBytes, st) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (ev) cudaEventRecord(ev[0], st);
+  if (plan->total_table_blocks > 0)
+    kb_tables<<<(unsigned)plan->total_table_blocks, kTabThreads, 0, st>>>(b);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (plan->total_chunks > 0) {
+    const int ti = plan->tuning.warp_table == 512 ? 0 : plan->tuning.warp_table == 1024 ? 1 : 2;
+    const long long cap = (long long)L->sms * L->kb_sample_blocks_per_sm[ti];
+    const int g = (int)std::min<long long>(plan->total_chunks, cap);
+    const size_t sm = (size_t)kDedupWarps * plan->tuning.warp_table * sizeof(int);
+    if (ti == 0) kb_sample<512><<<g, kDedupThreads, sm, st>>>(b);
+    else if (ti == 1) kb_sample<1024><<<g, kDedupThreads, sm, st>>>(b);
+    else kb_sample<2048><<<g, kDedupThreads, sm, st>>>(b);
+    if (ev) cudaEventRecord(ev[2], st);
+    kb_heavy<<<L->sms, kHeavyThreads, L->kb_heavy_dyn_smem, st>>>(b, L->kb_heavy_bitmap_words);
+  } else if (ev) {
+    cudaEventRecord(ev[2], st);
+  }
+  if (ev) cudaEventRecord(ev[3], st);
+  const long long cap = (long long)L->sms * plan->tuning.flop_blocks_per_sm;
+  const int g = (int)std::min<long long>(plan->total_tiles, cap);
+  prof_mark(false, st);
+  kb_flop<<<g, kFlopThreads, 0, st>>>(b);
+  prof_mark(true, st);
+  if (ev) cudaEventRecord(ev[4], st);
+  return cudaGetLastError() == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
+int batch_prepare(const spgemm_batch_item_t* items, int n, const spgemm_batch_tuning_t* tuning,
+                  spgemm_batch_plan_t* plan, void* ws, size_t ws_bytes, void* host_staging,
+                  size_t staging_bytes, int* bad_item, cudaStream_t st) {
+  if (!items || n <= 0 || n > SPGEMM_BATCH_MAX_CASES || !plan || !ws) return SPGEMM_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return SPGEMM_ERR_WORKSPACE;
+  // host checks first (tuning ranges, every case), then the device limits
+  spgemm_batch_tuning_t tu;
+  int rc = resolve_tuning(tuning, nullptr, &tu);
+  if (rc) return rc;
+  BatchTotals T;
+  int bad = -1;
+  if ((rc = batch_totals(items, n, tu.tile_items, tu.sample_chunk, &T, &bad))) {
+    if (bad_item && bad >= 0) *bad_item = bad;
+    return rc;
+  }
+  const BatchLayout l = layout_of(T, n);
+  if (ws_bytes < l.total) return SPGEMM_ERR_WORKSPACE;
+  const DeviceLimits* L = limits();
+  if (!L) return SPGEMM_ERR_CUDA;
+  if ((rc = resolve_tuning(&tu, L, &tu))) return rc;
+  std::vector<unsigned char> own;
+  unsigned char* buf = static_cast<unsigned char*>(host_staging);
+  if (buf) {
+    if (staging_bytes < l.plan_bytes()) return SPGEMM_ERR_INVALID_ARG;
+  } else {
+    own.resize(l.plan_bytes());
+    buf = own.data();
+  }
+  char* dev = static_cast<char*>(ws);
+  BatchCase* cs = reinterpret_cast<BatchCase*>(buf);
+  int* tile_case = reinterpret_cast<int*>(buf + (l.tile_case - l.cases));
+  int* chunk_case = reinterpret_cast<int*>(buf + (l.chunk_case - l.cases));
+  int* tab_case = reinterpret_cast<int*>(buf + (l.tab_case - l.cases));
+  long long row = 0, cand = 0, tile = 0, tab = 0, ch = 0;
+  size_t deg = l.deg;
+  for (int i = 0; i < n; ++i) {
+    const spgemm_batch_item_t& it = items[i];
+    long long nc = 0;
+    sample_candidates(&it.cfg, it.A.rows, &nc);
+    BatchCase& c = cs[i];
+    c.a_rpt = it.A.rpt;
+    c.a_col = it.A.col;
+    c.b_rpt = it.B.rpt;
+    c.b_col = it.B.col;
+    c.M = it.A.rows;
+    c.K = it.A.cols;
+    c.N = it.B.cols;
+    c.nnzA = it.A.nnz;
+    c.nnzB = it.B.nnz;
+    c.seed = it.cfg.seed;
+    c.threshold = it.cfg.threshold;
+    c.n_cand = nc;
+    c.cand_off = cand;
+    c.row_base = row;
+    c.tab_blk0 = tab;
+    c.pred = it.pred_row;
+    c.offsets = reinterpret_cast<long long*>(it.offsets);
+    c.flop = it.flop_row;
+    c.res = it.res;
+    c.deg8 = reinterpret_cast<unsigned char*>(dev + deg);
+    c.src = it.cfg.mode == SPGEMM_SAMPLE_BERNOULLI ? kSrcBernoulli : kSrcDraws;
+    c.vec_ok = ((reinterpret_cast<uintptr_t>(it.A.col) | reinterpret_cast<uintptr_t>(it.B.rpt)) & 15) == 0;
+    const long long nt = tiles_of(it, tu.tile_items);
+    c.tile0 = (int)tile;
+    c.ntiles = (int)nt;
+    for (long long q = 0; q < nt; ++q) tile_case[tile + q] = i;
+    const long long nb = tab_blocks_of(it);
+    for (long long q = 0; q < nb; ++q) tab_case[tab + q] = i;
+    // chunks whose first candidate falls in this case
+    for (; ch < T.chunks && ch * (long long)tu.sample_chunk < cand + nc; ++ch) chunk_case[ch] = i;
+    row += it.A.rows;
+    cand += nc;
+    tile += nt;
+    tab += nb;
+    deg += r16((size_t)it.A.cols + 16);
+  }
+  if (cudaMemcpyAsync(dev + l.cases, buf, l.plan_bytes(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return SPGEMM_ERR_CUDA;
+  if (cudaMemsetAsync(dev + l.acc, 0, sizeof(CaseAcc) * (size_t)n, st) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (!host_staging && cudaStreamSynchronize(st) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  spgemm_batch_plan_t p{};
+  p.n_cases = n;
+  p.total_rows = T.rows;
+  p.total_candidates = T.cand;
+  p.total_tiles = T.tiles;
+  p.total_chunks = T.chunks;
+  p.total_table_blocks = T.tab;
+  p.ws_bytes = l.total;
+  p.tuning = tu;
+  *plan = p;
+  return SPGEMM_OK;
 }
 
 }  // namespace
@@ -367,6 +666,122 @@ int spgemm_predict_structure_static(const spgemm_csr_t* A, const spgemm_csr_t* B
   if (cudaMemsetAsync(ws, 0, kStaticHeaderBytes, static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return SPGEMM_ERR_CUDA;
   return predict_common(A, B, cfg, pred_row, offsets, flop_row, res, ws, kStaticBytes, stream, false);
+}
+
+size_t spgemm_batch_workspace_size(const spgemm_batch_item_t* items, int32_t n) {
+  if (!items || n <= 0 || n > SPGEMM_BATCH_MAX_CASES) return 0;
+  BatchTotals T;
+  int bad = -1;
+  if (batch_totals(items, n, kMinTile, kMinChunk, &T, &bad)) return 0;
+  return layout_of(T, n).total;
+}
+
+size_t spgemm_batch_staging_size(const spgemm_batch_item_t* items, int32_t n) {
+  if (!items || n <= 0 || n > SPGEMM_BATCH_MAX_CASES) return 0;
+  BatchTotals T;
+  int bad = -1;
+  if (batch_totals(items, n, kMinTile, kMinChunk, &T, &bad)) return 0;
+  return layout_of(T, n).plan_bytes();
+}
+
+int spgemm_batch_prepare(const spgemm_batch_item_t* items, int32_t n,
+                         const spgemm_batch_tuning_t* tuning, spgemm_batch_plan_t* plan,
+                         void* ws, size_t ws_bytes, void* host_staging, size_t staging_bytes,
+                         int32_t* bad_item, void* stream) {
+  int bad = -1;
+  const int rc = batch_prepare(items, n, tuning, plan, ws, ws_bytes, host_staging, staging_bytes, &bad,
+                               static_cast<cudaStream_t>(stream));
+  if (rc && bad_item && bad >= 0) *bad_item = bad;
+  return rc;
+}
+
+int spgemm_predict_batch(const spgemm_batch_plan_t* plan, void* ws, size_t ws_bytes, void* stream) {
+  if (!plan || !ws || plan->n_cases <= 0 || plan->total_tiles <= 0) return SPGEMM_ERR_INVALID_ARG;
+  if (ws_bytes < plan->ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 255)) return SPGEMM_ERR_WORKSPACE;
+  const DeviceLimits* L = limits();
+  if (!L) return SPGEMM_ERR_CUDA;
+  spgemm_batch_tuning_t tu;
+  if (resolve_tuning(&plan->tuning, L, &tu)) return SPGEMM_ERR_INVALID_ARG;
+  return launch_batch(L, plan, ws, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+int spgemm_batch_autotune(const spgemm_batch_item_t* items, int32_t n, void* ws, size_t ws_bytes,
+                          int32_t reps, spgemm_batch_tuning_t* best, float* best_ms,
+                          spgemm_batch_plan_t* plan, void* stream) {
+  if (!best || !plan || reps < 1 || reps > 1000) return SPGEMM_ERR_INVALID_ARG;
+  const DeviceLimits* L = limits();
+  if (!L) return SPGEMM_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  // median over `reps` runs of the time between events a and b
+  auto measure = [&](const spgemm_batch_tuning_t& tu, int a, int b, float* out) -> int {
+    int rc = batch_prepare(items, n, &tu, plan, ws, ws_bytes, nullptr, 0, nullptr, st);
+    if (rc) return rc;
+    if ((rc = launch_batch(L, plan, ws, st, ev))) return rc;
+    std::vector<float> ts;
+    for (int r = 0; r < reps; ++r) {
+      if ((rc = launch_batch(L, plan, ws, st, ev))) return rc;
+      if (cudaEventSynchronize(ev[4]) != cudaSuccess) return SPGEMM_ERR_CUDA;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[a], ev[b]) != cudaSuccess) return SPGEMM_ERR_CUDA;
+      ts.push_back(ms);
+    }
+    std::sort(ts.begin(), ts.end());
+    *out = ts[ts.size() / 2];
+    return SPGEMM_OK;
+  };
+  int rc = SPGEMM_OK;
+  spgemm_batch_tuning_t cur{};
+  float t_best = 0.f;
+  // 1) the sampled-row passes: table size, heavy threshold, chunk size
+  bool first = true;
+  const int tables[3] = {512, 1024, 2048};
+  const int chunks[3] = {8192, 32768, 131072};
+  for (int ti = 0; ti < 3 && !rc; ++ti) {
+    for (int hi = 0; hi < 2 && !rc; ++hi) {
+      for (int ci = 0; ci < 3 && !rc; ++ci) {
+        spgemm_batch_tuning_t tu{};
+        tu.warp_table = tables[ti];
+        tu.heavy_threshold = hi == 0 ? tables[ti] / 4 : tables[ti] / 2;
+        tu.sample_chunk = chunks[ci];
+        float ms = 0.f;
+        if ((rc = measure(tu, 1, 3, &ms))) break;
+        if (first || ms < t_best) {
+          cur = tu;
+          t_best = ms;
+          first = false;
+        }
+      }
+    }
+  }
+  // 2) the FLOP pass: tile size and blocks per SM
+  first = true;
+  const int tiles[5] = {4096, 8192, 16384, 32768, 65536};
+  spgemm_batch_tuning_t pick = cur;
+  for (int ti = 0; ti < 5 && !rc; ++ti) {
+    for (int bps = L->kb_flop_blocks_per_sm; bps >= 1 && bps >= L->kb_flop_blocks_per_sm - 2 && !rc; --bps) {
+      spgemm_batch_tuning_t tu = cur;
+      tu.tile_items = tiles[ti];
+      tu.flop_blocks_per_sm = bps;
+      float ms = 0.f;
+      if ((rc = measure(tu, 3, 4, &ms))) break;
+      if (first || ms < t_best) {
+        pick = tu;
+        t_best = ms;
+        first = false;
+      }
+    }
+  }
+  // 3) the pick, end to end; the workspace is left prepared with it
+  float total = 0.f;
+  if (!rc) rc = measure(pick, 0, 4, &total);
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  if (rc) return rc;
+  *best = pick;
+  if (best_ms) *best_ms = total;
+  return SPGEMM_OK;
 }
 
 int spgemm_set_profile_events(void* before, void* after) {

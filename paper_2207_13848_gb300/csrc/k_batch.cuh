@@ -1,0 +1,522 @@
+// Batched structure prediction: many independent predictions ("cases") of
+// uneven sizes run as four persistent launches, each spanning every case of
+// the batch (the method of each case is the single-case one: sample, exact nnz
+// of the sampled rows, compression ratio, FLOP per row, prediction and scan):
+//   kb_tables - the B row-length byte tables of all cases, with validation of
+//               B's offsets;
+//   kb_sample - the sample of every case and the exact nnz of its rows (warp
+//               per row), from chunks of the concatenated candidate sequence
+//               claimed one at a time; heavy rows of all cases share one queue;
+//   kb_heavy  - the queued rows of all cases, one block per row, claimed one at
+//               a time;
+//   kb_flop   - FLOP per row, prediction and allocation offsets for every case,
+//               from tiles of each case's merged sequence claimed one at a time;
+//               the scan across a case's tiles is a decoupled look-back (Merrill
+//               and Garland, "Single-pass parallel prefix scan with decoupled
+//               look-back", NVIDIA tech. report NVR-2016-002).
+// Work is claimed in increasing order and a tile only ever waits for tiles of
+// lower index (its predecessors in the same case), which were claimed earlier
+// by running blocks; so no wait can deadlock, whatever the number of blocks
+// resident at once.  The kernel boundaries order the phases: every case's
+// sample totals are final before the first FLOP tile starts.
+#pragma once
+
+#include "common.cuh"
+#include "k_dedup.cuh"
+#include "k_flop.cuh"
+
+namespace spg {
+
+// One case as planned on the host (written into the workspace by the prepare
+// call).  Candidates, tiles and table blocks of all cases are numbered in case
+// order.
+struct BatchCase {
+  const int* a_rpt;
+  const int* a_col;
+  const int* b_rpt;
+  const int* b_col;
+  long long M, K, N, nnzA, nnzB;
+  unsigned long long seed, threshold;  // sample: hash seed and Bernoulli threshold
+  long long n_cand;                    // candidates of the sample (rows or draws)
+  long long cand_off;                  // index of the first one in the batch
+  long long row_base;                  // batch-wide id of row 0 (heavy queue)
+  long long tab_blk0;                  // first kb_tables block of the case
+  int* pred;                           // [M]
+  long long* offsets;                  // [M + 1]
+  int* flop;                           // [M] or null
+  spgemm_result_t* res;
+  unsigned char* deg8;                 // [K] byte table, 16-byte aligned
+  int src;                             // kSrcBernoulli or kSrcDraws
+  int vec_ok;                          // A.col 16-byte aligned
+  int tile0, ntiles;                   // FLOP tiles [tile0, tile0 + ntiles), ntiles >= 1
+};
+
+// Per-case accumulators; zero between runs (the case's last tile resets them).
+struct alignas(64) CaseAcc {
+  unsigned long long f;  // f*: FLOP of the sampled rows
+  unsigned long long z;  // z*: nnz of the sampled rows
+  unsigned long long s;  // |S|
+  unsigned long long F;  // total FLOP
+  unsigned int status;   // SPGEMM_STATUS_* bits
+  unsigned int tiles_done;
+  unsigned int pad[6];
+};
+
+struct alignas(128) BatchHeader {
+  // work counters, zeroed before every run
+  unsigned long long sample_ctr;  // candidate chunks claimed
+  unsigned int heavy_count;       // rows queued for kb_heavy
+  unsigned int heavy_ctr;         // queued rows claimed
+  unsigned int tile_ctr;          // FLOP tiles claimed
+  unsigned int tiles_done;        // FLOP tiles finished
+  unsigned int pad0[10];
+  // flag epoch of the last completed run (only grows)
+  unsigned int epoch;
+  unsigned int pad1[15];
+};
+constexpr size_t kBatchCounterBytes = 64;  // the leading counters of BatchHeader
+
+constexpr int kTabRowsPerBlock = 4096;  // B rows per kb_tables block (4 per thread-word, 4 words per thread)
+constexpr int kTabThreads = 256;
+
+struct BatchArgs {
+  BatchHeader* hdr;
+  const BatchCase* cases;
+  CaseAcc* acc;
+  Slot* slots;               // [total_tiles]
+  const int* tile_case;      // [total_tiles] case of each tile
+  const int* chunk_case;     // [total_chunks] case of each chunk's first candidate
+  const int* tab_case;       // [total_tab_blocks] case of each table block
+  int* heavy;                // [heavy_cap] batch-wide row ids queued for kb_heavy
+  int n_cases;
+  int total_tiles;
+  long long total_cand;
+  long long total_chunks;
+  long long sample_chunk;    // candidates per chunk
+  long long heavy_cap;
+  int heavy_thr;             // products per row above which a row is queued
+};
+
+// Index of the last case i with key(i) <= x, for keys that never decrease with
+// i and key(0) <= x: one warp, 32 probes per step.
+template <class Key>
+__device__ __forceinline__ int warp_last_le(int n, long long x, Key key) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = n;  // key(lo) <= x, and key(hi) > x or hi == n
+  while (hi - lo > 1) {
+    const int step = (hi - lo + 31) / 32;
+    const int p = lo + (lane + 1) * step;
+    const bool le = p < hi && key(p) <= x;
+    const int k = __popc(__ballot_sync(kFull, le));
+    const int nlo = lo + k * step;
+    hi = min(hi, nlo + step);
+    lo = nlo;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// B row-length tables of every case (see k_degree_table), kTabRowsPerBlock
+// rows of one case per block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTabThreads) kb_tables(BatchArgs b) {
+  const int c = __ldg(b.tab_case + blockIdx.x);
+  const BatchCase& k = b.cases[c];
+  const long long K = k.K, nnzB = k.nnzB;
+  const long long r0 = (blockIdx.x - k.tab_blk0) * (long long)kTabRowsPerBlock;
+  bool bad = false;
+  for (long long k0 = r0 + threadIdx.x * 4; k0 < min(K, r0 + kTabRowsPerBlock); k0 += kTabThreads * 4) {
+    unsigned word = 0;
+    long long prev = __ldg(k.b_rpt + k0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (k0 + u < K) {
+        const long long next = __ldg(k.b_rpt + k0 + u + 1);
+        long long d = next - prev;
+        if (d < 0 || prev < 0 || next > nnzB) {
+          bad = true;
+          d = 0;
+        }
+        word |= (unsigned)(d < kDegEscape ? d : kDegEscape) << (8 * u);
+        prev = next;
+      }
+    }
+    *reinterpret_cast<unsigned*>(k.deg8 + k0) = word;
+  }
+  if (bad) atomicOr(&b.acc[c].status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
+}
+
+// Fills the per-warp (or per-block) deduplication arguments of case c.
+__device__ __forceinline__ void batch_dedup_args(const BatchArgs& b, int c, DedupArgs& d) {
+  const BatchCase& k = b.cases[c];
+  d.M = k.M;
+  d.K = k.K;
+  d.N = k.N;
+  d.nnzA = k.nnzA;
+  d.nnzB = k.nnzB;
+  d.a_rpt = k.a_rpt;
+  d.a_col = k.a_col;
+  d.b_rpt = k.b_rpt;
+  d.b_col = k.b_col;
+  d.src = k.src;
+  d.seed = k.seed;
+  d.threshold = k.threshold;
+  d.n_cand = k.n_cand;
+  d.nnz_out = nullptr;
+  d.status = &b.acc[c].status;
+  d.heavy_count = &b.hdr->heavy_count;
+  d.heavy = b.heavy;
+  d.heavy_cap = b.heavy_cap;
+  d.heavy_base = (int)k.row_base;
+  d.heavy_thr = b.heavy_thr;
+}
+
+// ---------------------------------------------------------------------------
+// Samples of all cases and the exact nnz of their rows.  A block claims a
+// chunk of the concatenated candidates, hashes them (each thread walking
+// forward through the cases its candidates fall in), stages the selected
+// (case, row) pairs in shared memory and hands them to its warps; a warp adds
+// its rows' FLOP / nnz / count to the case's accumulators when it moves on to
+// another case.  TABLE = hash slots per warp (>= 2 * heavy_thr).
+// ---------------------------------------------------------------------------
+template <int TABLE>
+__global__ void __launch_bounds__(kDedupThreads) kb_sample(BatchArgs b) {
+  extern __shared__ int dyn[];
+  __shared__ int list_row[kListCap];
+  __shared__ int list_case[kListCap];
+  __shared__ DedupArgs wa[kDedupWarps];
+  __shared__ int list_n;
+  __shared__ long long s_chunk;
+  __shared__ int s_case;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  int* tbl = dyn + warp * TABLE;
+  int cur = -1;  // the warp's current case
+  long long f_loc = 0, z_loc = 0, s_loc = 0;
+  auto flush = [&]() {
+    if (lane == 0 && cur >= 0) {
+      CaseAcc& A = b.acc[cur];
+      if (f_loc) atomicAdd(&A.f, (unsigned long long)f_loc);
+      if (z_loc) atomicAdd(&A.z, (unsigned long long)z_loc);
+      if (s_loc) atomicAdd(&A.s, (unsigned long long)s_loc);
+    }
+    f_loc = z_loc = s_loc = 0;
+  };
+  for (;;) {
+    if (t == 0) {
+      const long long ch = (long long)atomicAdd(&b.hdr->sample_ctr, 1ull);
+      s_chunk = ch;
+      if (ch < b.total_chunks) s_case = __ldg(b.chunk_case + ch);
+    }
+    __syncthreads();
+    const long long chunk = s_chunk;
+    if (chunk >= b.total_chunks) break;
+    long long base = chunk * b.sample_chunk;
+    const long long c_end = min(b.total_cand, base + b.sample_chunk);
+    // this thread's case, and its candidate range [lo_x, hi_x)
+    int cx = s_case;
+    long long lo_x = b.cases[cx].cand_off, hi_x = lo_x + b.cases[cx].n_cand;
+    while (base < c_end) {
+      if (t == 0) list_n = 0;
+      __syncthreads();
+      for (;;) {
+        const long long x = base + t;
+        bool take = false;
+        int row = 0;
+        // (every candidate below total_cand lies in some case, so the walk
+        // stops inside the array; the bound only guards a corrupted plan)
+        while (x < c_end && x >= hi_x && cx + 1 < b.n_cases) {
+          ++cx;
+          lo_x = b.cases[cx].cand_off;
+          hi_x = lo_x + b.cases[cx].n_cand;
+        }
+        if (x < c_end && x >= lo_x && x < hi_x) {
+          const BatchCase& k = b.cases[cx];
+          const unsigned long long loc = (unsigned long long)(x - lo_x);
+          const uint32_t h = sample_hash32(k.seed, loc);
+          if (k.src == kSrcBernoulli) {
+            take = (uint64_t)h < k.threshold;
+            row = (int)loc;
+          } else {
+            take = true;
+            row = (int)(((uint64_t)h * (uint64_t)k.M) >> 32);
+          }
+        }
+        const unsigned bal = __ballot_sync(kFull, take);
+        int wbase = 0;
+        if (lane == 0 && bal) wbase = atomicAdd(&list_n, __popc(bal));
+        wbase = __shfl_sync(kFull, wbase, 0);
+        if (take) {
+          const int e = wbase + __popc(bal & ((1u << lane) - 1u));
+          list_row[e] = row;
+          list_case[e] = cx;
+        }
+        base += kDedupThreads;
+        __syncthreads();
+        if (base >= c_end || list_n > kListCap - kDedupThreads) break;
+      }
+      const int n = list_n;
+      for (int e = warp; e < n; e += kDedupWarps) {
+        const int c = list_case[e], r = list_row[e];
+        if (c != cur) {
+          flush();
+          cur = c;
+          if (lane == 0) batch_dedup_args(b, c, wa[warp]);
+          __syncwarp();
+        }
+        long long flop;
+        const long long nnz = dedup_row_warp(wa[warp], r, tbl, &flop);
+        if (lane == 0) {
+          f_loc += flop;
+          s_loc += 1;
+          if (nnz >= 0) z_loc += nnz;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  flush();
+}
+
+// ---------------------------------------------------------------------------
+// Heavy rows of all cases, one block per row (see heavy_row_nnz).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kHeavyThreads) kb_heavy(BatchArgs b, int bitmap_words) {
+  extern __shared__ unsigned tab[];
+  __shared__ HeavySmem sm;
+  __shared__ DedupArgs ha;
+  __shared__ unsigned s_h;
+  __shared__ int s_case;
+  const int t = threadIdx.x;
+  const unsigned n_heavy = (unsigned)min((long long)b.hdr->heavy_count, b.heavy_cap);
+  for (;;) {
+    if (t == 0) s_h = atomicAdd(&b.hdr->heavy_ctr, 1u);
+    __syncthreads();
+    const unsigned h = s_h;
+    if (h >= n_heavy) break;
+    const int g = b.heavy[h];
+    if (t < 32) {
+      const int c = warp_last_le(b.n_cases, (long long)g, [&](int i) { return b.cases[i].row_base; });
+      if (t == 0) {
+        s_case = c;
+        batch_dedup_args(b, c, ha);
+      }
+    }
+    __syncthreads();
+    const int c = s_case;
+    bool bad = false;
+    const long long nnz = heavy_row_nnz(ha, g - ha.heavy_base, sm, tab, bitmap_words, bad);
+    if (t == 0) atomicAdd(&b.acc[c].z, (unsigned long long)nnz);
+    if (__syncthreads_or(bad) && t == 0) atomicOr(&b.acc[c].status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive prefix of `tile` over the tiles [first, tile) of its case, by one
+// warp: each lane watches one predecessor, 32 at a time going backwards, until
+// one of them has published its inclusive prefix (ftot_flag; the case's first
+// tile publishes it at once) - the aggregates (total_flag) of the tiles after
+// it are added on.  Waits give up after about a second each and set TIMEOUT.
+// ---------------------------------------------------------------------------
+__device__ long long lookback_excl(Slot* slots, int first, int tile, unsigned ep, unsigned* status) {
+  const int lane = threadIdx.x & 31;
+  long long excl = 0;
+  for (int hi = tile - 1; hi >= first; hi -= 32) {
+    const int q = hi - lane;
+    int st = 0;
+    long long v = 0;
+    if (q >= first) {
+      const uint64_t t0 = global_ns();
+      unsigned ns = 32;
+      for (int it = 0; it < (1 << 26); ++it) {
+        if (flag_load(&slots[q].ftot_flag) == ep) {
+          st = 2;
+          v = *reinterpret_cast<volatile long long*>(&slots[q].ftot);
+          break;
+        }
+        if (flag_load(&slots[q].total_flag) == ep) {
+          st = 1;
+          v = *reinterpret_cast<volatile long long*>(&slots[q].total);
+          break;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+        if ((it & 63) == 63 && global_ns() - t0 > 1000000000ull) {
+          atomicOr(status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);
+          st = 2;  // stop here
+          break;
+        }
+      }
+    }
+    const unsigned incl = __ballot_sync(kFull, st == 2);
+    const int stop = incl ? __ffs(incl) - 1 : 31;
+    excl += warp_sum((lane <= stop && q >= first) ? v : 0ll);
+    if (incl) break;
+  }
+  return excl;
+}
+
+// ---------------------------------------------------------------------------
+// FLOP per row, prediction and offsets of all cases, tile by tile.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) kb_flop(BatchArgs b) {
+  __shared__ FlopShared sm;
+  __shared__ FlopArgs fa;
+  __shared__ int s_tile, s_case, s_tile0, s_ntiles;
+  const int t = threadIdx.x;
+  BatchHeader* hdr = b.hdr;
+  const unsigned ep = *reinterpret_cast<volatile unsigned*>(&hdr->epoch) + 1u;
+  Slot* slots = b.slots;
+  for (;;) {
+    if (t == 0) {
+      const int tile = (int)atomicAdd(&hdr->tile_ctr, 1u);
+      s_tile = tile;
+      if (tile < b.total_tiles) {
+        const int c = __ldg(b.tile_case + tile);
+        const BatchCase& k = b.cases[c];
+        s_case = c;
+        s_tile0 = k.tile0;
+        s_ntiles = k.ntiles;
+        fa.M = k.M;
+        fa.K = k.K;
+        fa.nnzA = k.nnzA;
+        fa.nnzB = k.nnzB;
+        fa.a_rpt = k.a_rpt;
+        fa.a_col = k.a_col;
+        fa.b_rpt = k.b_rpt;
+        fa.deg8 = k.deg8;
+        fa.flop = k.flop;
+        fa.pred = k.pred;
+        fa.offsets = k.offsets;
+        fa.vec_ok = k.vec_ok;
+        fa.res = k.res;
+      }
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= b.total_tiles) break;
+    const int c = s_case, tile0 = s_tile0, nt = s_ntiles, lt = tile - tile0;
+    CaseAcc& acc = b.acc[c];
+    unsigned* status = &acc.status;
+    const long long M = fa.M;
+    const long long D = M + fa.nnzA;
+    const long long d0 = D * lt / nt, d1 = D * (lt + 1) / nt;
+    const unsigned long long fz = acc.f, zz = acc.z;
+    const double ratio = fz ? (double)zz / (double)fz : 0.0;
+
+    bool bad = false;
+    long long ftot = 0, ptot = 0;
+    flop_range<kModePredict>(fa, d0, d1, lt > 0, fz, zz, ratio, sm, &sm.out, ftot, ptot, bad);
+    if (__syncthreads_or(bad) && t == 0) atomicOr(status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
+    const int i0 = sm.out.i0, i1 = sm.out.i1;
+
+    // ---- carries between the tiles of the case (waits only on tile - 1)
+    if (t == 0) {
+      const long long run = sm.out.run, head_known = sm.out.head_known;
+      long long extra_f = sm.out.extra_f, extra_p = sm.out.extra_p;
+      if (sm.out.dep) {
+        long long cin = 0;
+        if (flag_wait(&slots[tile - 1].carry_flag, ep, status)) cin = slots[tile - 1].carry;
+        slots[tile].carry = cin + run;
+        flag_store(&slots[tile].carry_flag, ep);
+      } else {
+        slots[tile].carry = i1 < M ? run : 0;
+        flag_store(&slots[tile].carry_flag, ep);
+        if (sm.out.head_pending) {
+          long long cin = 0;
+          if (flag_wait(&slots[tile - 1].carry_flag, ep, status)) cin = slots[tile - 1].carry;
+          const long long v = cin + head_known;
+          const int p = fz == 0 ? (int)v : pred_proposed((uint32_t)v, zz, fz, ratio);
+          fa.pred[i0] = p;
+          if (fa.flop) fa.flop[i0] = (int)v;
+          extra_f += v;
+          extra_p += p;
+        }
+      }
+      sm.bc[4] = extra_f;
+      sm.bc[5] = extra_p;
+    }
+    __syncthreads();
+    const long long blk_f = block_sum<kFlopThreads>(ftot, sm.red) + sm.bc[4];
+    const long long blk_p = block_sum<kFlopThreads>(ptot, sm.red) + sm.bc[5];
+
+    // ---- exclusive prefix of the tile within its case
+    if (t < 32) {
+      if (t == 0) {
+        if (lt == 0) {
+          slots[tile].ftot = blk_p;
+          flag_store(&slots[tile].ftot_flag, ep);
+        } else {
+          slots[tile].total = blk_p;
+          flag_store(&slots[tile].total_flag, ep);
+        }
+      }
+      const long long excl = lt > 0 ? lookback_excl(slots, tile0, tile, ep, status) : 0;
+      if (t == 0) {
+        if (lt > 0) {
+          slots[tile].ftot = excl + blk_p;
+          flag_store(&slots[tile].ftot_flag, ep);
+        }
+        sm.bc[6] = excl;
+      }
+    }
+    __syncthreads();
+    long long run = sm.bc[6];
+
+    // ---- offsets of the rows [i0, i1)
+    for (int rb = i0; rb < i1; rb += kFlopThreads * kRowsPerThread) {
+      const int r0 = rb + t * kRowsPerThread;
+      int pv[kRowsPerThread];
+      long long loc = 0;
+#pragma unroll
+      for (int u = 0; u < kRowsPerThread; ++u) {
+        pv[u] = (r0 + u < i1) ? fa.pred[r0 + u] : 0;
+        loc += pv[u];
+      }
+      long long tot;
+      long long ex = block_excl_scan<kFlopThreads>(loc, sm.red, &tot) + run;
+#pragma unroll
+      for (int u = 0; u < kRowsPerThread; ++u) {
+        if (r0 + u < i1) {
+          fa.offsets[r0 + u] = ex;
+          ex += pv[u];
+        }
+      }
+      run += tot;
+    }
+
+    // ---- the case's last tile writes offsets[M]; its last finisher the result
+    if (t == 0) {
+      if (lt == nt - 1) fa.offsets[M] = run;
+      atomicAdd(&acc.F, (unsigned long long)blk_f);
+      __threadfence();
+      const unsigned prev = atomicAdd(&acc.tiles_done, 1u);
+      if (prev == (unsigned)nt - 1) {
+        __threadfence();
+        volatile CaseAcc* va = &acc;
+        unsigned st = va->status;
+        if (va->f == 0) st |= SPGEMM_STATUS_WARN_EMPTY_SAMPLE;
+        spgemm_result_t* res = fa.res;
+        res->flop_total = (long long)va->F;
+        res->flop_s = (long long)va->f;
+        res->nnz_s = (long long)va->z;
+        res->n_sampled = (long long)va->s;
+        res->pred_total = *reinterpret_cast<volatile long long*>(&slots[tile0 + nt - 1].ftot);
+        res->status = (int)st;
+        va->f = 0;
+        va->z = 0;
+        va->s = 0;
+        va->F = 0;
+        va->status = 0;
+        va->tiles_done = 0;
+      }
+      __threadfence();
+      if (atomicAdd(&hdr->tiles_done, 1u) == (unsigned)b.total_tiles - 1) {
+        __threadfence();
+        *reinterpret_cast<volatile unsigned*>(&hdr->epoch) = ep;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace spg

@@ -2,8 +2,8 @@
 // loop of Algorithm 2, Sec. V-B), re-designed for the GPU:
 //   - rows with at most 32 products: one warp holds every product in a lane and
 //     counts distinct column ids with __match_any_sync (no memory table);
-//   - rows with at most kWarpCap products: one warp, open-addressing table in the
-//     warp's slice of shared memory;
+//   - rows with at most heavy_thr products (kWarpCap by default): one warp,
+//     open-addressing table in the warp's slice of shared memory;
 //   - heavier rows are queued and handled by a whole thread block, with a
 //     shared-memory hash table (up to kBlockHashCap products) or a bitmap over
 //     the columns of B (split into column ranges when N exceeds its capacity).
@@ -39,11 +39,15 @@ struct DedupArgs {
   int64_t n_cand;      // candidates: M (Bernoulli, all rows) or the number of draws
   int* nnz_out;        // all-rows mode: nnz per row (int32[M]); otherwise null
   Workspace ws;
-  // heavy-row queue: ws.heavy (capacity heavy_cap), plus the case id of each
-  // entry in heavy_case when several predictions share the queue (else null)
+  unsigned int* status;  // where SPGEMM_STATUS_* bits go (the header's, or a batch case's)
+  // Rows with more than heavy_thr products (at most half the warp table) are
+  // queued for the block-per-row pass: heavy[atomicAdd(heavy_count, 1)] =
+  // heavy_base + row, while fewer than heavy_cap entries are queued.
+  unsigned int* heavy_count;
+  int* heavy;
   long long heavy_cap;
-  int* heavy_case;
-  int case_id;
+  int heavy_base;
+  int heavy_thr;
 };
 
 __device__ __forceinline__ uint32_t mix_key(int key) { return (uint32_t)key * 0x9E3779B1u; }
@@ -81,9 +85,10 @@ __device__ __forceinline__ void b_row(const DedupArgs& a, int k, long long& s, l
   len = e - b;
 }
 
-// One warp computes flop and (unless the row is heavy) nnz of `row`.
-// Returns nnz, or -1 when the row was queued for the heavy pass.  flop is
-// returned through *flop_out (same value on every lane).
+// One warp computes flop and (unless the row is heavy) nnz of `row`, with a
+// table `tbl` of at least 2 * a.heavy_thr slots.  Returns nnz, or -1 when the
+// row was queued for the heavy pass.  flop is returned through *flop_out (same
+// value on every lane).
 __device__ long long dedup_row_warp(const DedupArgs& a, int row, int* tbl, long long* flop_out) {
   const int lane = threadIdx.x & 31;
   bool bad = false;
@@ -104,7 +109,7 @@ __device__ long long dedup_row_warp(const DedupArgs& a, int row, int* tbl, long 
     flop += len;
   }
   flop = warp_sum(flop);
-  if (__any_sync(kFull, bad) && lane == 0) set_status(a.ws.hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
   *flop_out = flop;
   if (flop == 0) return 0;
 
@@ -133,7 +138,7 @@ __device__ long long dedup_row_warp(const DedupArgs& a, int row, int* tbl, long 
     return __popc(__ballot_sync(kFull, leader));
   }
 
-  if (flop <= kWarpCap) {
+  if (flop <= a.heavy_thr) {
     const int lg = max(6, ceil_log2((uint32_t)(2 * flop)));
     const int P = 1 << lg;
     for (int i = lane; i < P; i += 32) tbl[i] = -1;
@@ -177,11 +182,8 @@ __device__ long long dedup_row_warp(const DedupArgs& a, int row, int* tbl, long 
   }
 
   if (lane == 0) {
-    const unsigned h = atomicAdd(&a.ws.hdr->heavy_count, 1u);
-    if (h < (unsigned long long)a.heavy_cap) {
-      a.ws.heavy[h] = row;
-      if (a.heavy_case) a.heavy_case[h] = a.case_id;
-    }
+    const unsigned h = atomicAdd(a.heavy_count, 1u);
+    if (h < (unsigned long long)a.heavy_cap) a.heavy[h] = a.heavy_base + row;
   }
   return -1;
 }
@@ -354,16 +356,16 @@ __device__ long long heavy_row_nnz(const DedupArgs& a, int row, HeavySmem& sm, u
 __global__ void __launch_bounds__(kHeavyThreads) k_dedup_heavy(DedupArgs a, int bitmap_words) {
   extern __shared__ unsigned tab[];
   __shared__ HeavySmem sm;
-  const unsigned n_heavy = (unsigned)min((long long)a.ws.hdr->heavy_count, a.heavy_cap);
+  const unsigned n_heavy = (unsigned)min((long long)*a.heavy_count, a.heavy_cap);
   for (unsigned h = blockIdx.x; h < n_heavy; h += gridDim.x) {
-    const int row = a.ws.heavy[h];
+    const int row = a.heavy[h];
     bool bad = false;
     const long long nnz = heavy_row_nnz(a, row, sm, tab, bitmap_words, bad);
     if (threadIdx.x == 0) {
       atomicAdd(&a.ws.hdr->z_acc, (unsigned long long)nnz);
       if (a.nnz_out) a.nnz_out[row] = (int)nnz;
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(a.ws.hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
   }
 }
 

@@ -54,9 +54,13 @@ def test_status_strings(lib):
 
 
 def test_struct_layouts_match_header():
+    # the library asserts the same sizes at compile time
     assert ctypes.sizeof(sp.CsrStruct) == 40
     assert ctypes.sizeof(sp.ConfigStruct) == 32
     assert sp.RESULT_BYTES == 48
+    assert ctypes.sizeof(sp.BatchItemStruct) == 144
+    assert ctypes.sizeof(sp.TuningStruct) == 32
+    assert ctypes.sizeof(sp.PlanStruct) == 88
 
 
 def test_workspace_size_grows_with_rows(lib):
@@ -114,6 +118,69 @@ def test_host_errors(lib):
     cfgd = sp.config(mode=sp.SAMPLE_PAPER_DRAW, sample_num=10)
     assert lib.spgemm_sample_rows(100, ctypes.byref(cfgd), 0x4000, 5, 0x3000, 0x10000, ws, None) \
         == sp.ERR_INVALID_ARG
+
+
+def _items(lib, shapes, cfg=None):
+    """Batch items with fake device addresses (never dereferenced by host checks)."""
+    items = (sp.BatchItemStruct * len(shapes))()
+    for i, (a, b) in enumerate(shapes):
+        items[i].A, items[i].B = _Fake(*a).struct(), _Fake(*b).struct()
+        items[i].cfg = cfg or sp.config(ratio=0.01)
+        items[i].pred_row, items[i].offsets, items[i].res = 0x4000, 0x5000, 0x3000
+    return items
+
+
+class _FakeWs:
+    def __init__(self, addr, nbytes):
+        self.addr, self.nbytes = addr, nbytes
+
+    def ptr(self):
+        return ctypes.c_void_p(self.addr)
+
+
+def _prepare(lib, items, n, tuning, plan, ws, staging, bad):
+    assert staging is None
+    return lib.spgemm_batch_prepare(items, n, ctypes.byref(tuning) if tuning is not None else None,
+                                    ctypes.byref(plan), ws.ptr(), ws.nbytes, None, 0,
+                                    ctypes.byref(bad) if bad is not None else None, None)
+
+
+def test_batch_workspace_and_staging_sizes(lib):
+    one = _items(lib, [((100, 50, 300), (50, 70, 200))])
+    two = _items(lib, [((100, 50, 300), (50, 70, 200)), ((1 << 20, 1 << 20, 1 << 24), ((1 << 20), 9, 5))])
+    s1, s2 = sp.spgemm_batch_workspace_size(one, 1), sp.spgemm_batch_workspace_size(two, 2)
+    assert s1 > 0 and s2 > s1 + 4 * (1 << 20) + (1 << 20)
+    assert sp.spgemm_batch_staging_size(two, 2) >= 64 * 2
+    assert sp.spgemm_batch_workspace_size(one, 0) == 0
+    assert sp.spgemm_batch_workspace_size(_items(lib, [((100, 50, 300), (51, 70, 200))]), 1) == 0
+
+
+def test_batch_host_errors(lib):
+    shapes = [((100, 50, 300), (50, 70, 200))] * 2 + [((100, 50, 300), (51, 70, 200))]
+    items = _items(lib, shapes)
+    good = _items(lib, shapes[:2])
+    need = sp.spgemm_batch_workspace_size(good, 2)
+    ws = _FakeWs(0x100000, need)
+    plan, bad = sp.PlanStruct(), ctypes.c_int32(-1)
+    assert _prepare(lib, items, 3, None, plan, ws, None, bad) == sp.ERR_DIM_MISMATCH and bad.value == 2
+    assert _prepare(lib, items, 0, None, plan, ws, None, None) == sp.ERR_INVALID_ARG
+    assert _prepare(lib, good, 2, None, plan, _FakeWs(0x100010, need), None, None) == sp.ERR_WORKSPACE
+    assert _prepare(lib, good, 2, None, plan, _FakeWs(0x100000, need - 256), None, None) \
+        == sp.ERR_WORKSPACE
+    for bad_tuning in (dict(warp_table=300), dict(warp_table=512, heavy_threshold=257),
+                       dict(heavy_threshold=16), dict(tile_items=1000), dict(sample_chunk=5000),
+                       dict(flop_blocks_per_sm=-1)):
+        assert _prepare(lib, good, 2, sp.tuning(**bad_tuning), plan, ws, None, None) \
+            == sp.ERR_INVALID_ARG, bad_tuning
+    t = sp.tuning()
+    t.reserved[1] = 1
+    assert _prepare(lib, good, 2, t, plan, ws, None, None) == sp.ERR_INVALID_ARG
+    nopred = _items(lib, shapes[:1])
+    nopred[0].pred_row = None
+    assert _prepare(lib, nopred, 1, None, plan, ws, None, bad) == sp.ERR_INVALID_ARG
+    draws = _items(lib, shapes[:1], sp.config(mode=sp.SAMPLE_PAPER_DRAW, sample_num=101))
+    assert _prepare(lib, draws, 1, None, plan, ws, None, bad) == sp.ERR_INVALID_ARG
+    assert lib.spgemm_predict_batch(None, ws.ptr(), need, None) == sp.ERR_INVALID_ARG
 
 
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
