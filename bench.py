@@ -10,8 +10,8 @@ L2 is flushed (512 MiB write) before every timed step, since the operands
 (71 MB) fit in the 129 MB L2.
 
 Prints one JSON line.  Other keys: the roofline of the dominant kernel (the
-fused FLOP/prediction/scan kernel, timed with CUDA events on its stream through
-the library's profiling hook), the end-to-end number through the public API
+single-launch predictor, k_predict, which is the whole call; timed with CUDA
+events on its stream through the library's profiling hook), the end-to-end number through the public API
 with host buffers, the GPU exact symbolic phase on the same input, the
 prediction errors (Sec. VI-A), the CPU oracle baseline and the SM clocks.
 
@@ -160,16 +160,16 @@ def measured_peaks():
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_13848_gb300", "csrc")
-    for name in ("common.cuh", "k_flop.cuh"):
+    for name in ("common.cuh", "k_flop.cuh", "k_dedup.cuh", "k_predict.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    """DRAM bytes per launch of k_predict from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_flop_pred_predict_er_n2e20.md")
+    path = os.path.join(ROOT, "profiles", "k_predict_er_n2e20.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -180,13 +180,12 @@ def profiled_traffic():
 
 
 def algorithmic_bytes(A, f_s, n_s):
-    """Minimum bytes of one prediction (fused kernel; whole call).
-    Fused kernel: A.rpt, A.col, B.rpt (each once), pred (int32), offsets (int64).
-    Whole call adds the sampled rows' B column ids and their A offsets."""
+    """Minimum bytes one prediction must move: A.rpt, A.col and B.rpt once each,
+    pred (int32) and offsets (int64) written once, and for the sample the B
+    column ids of the sampled rows' products and the sampled rows' A offsets.
+    The call is one launch, so this is also the kernel's figure."""
     M, nnz, K = A.rows, A.nnz, A.cols
-    kern = 4 * (M + 1) + 4 * nnz + 4 * (K + 1) + 4 * M + 8 * (M + 1)
-    call = kern + 4 * f_s + 8 * n_s
-    return kern, call
+    return 4 * (M + 1) + 4 * nnz + 4 * (K + 1) + 4 * M + 8 * (M + 1) + 4 * f_s + 8 * n_s
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
@@ -373,7 +372,7 @@ def run_ours(args):
     est = estimates(r["flop_total"], sr["pred_total"], r["flop_s"], r["nnz_s"], M, r["n_sampled"])
     rowerr = row_errors(pred.cpu().numpy(), nnz_row.cpu().numpy())
 
-    kern_bytes, call_bytes = algorithmic_bytes(A, r["flop_s"], r["n_sampled"])
+    kern_bytes = call_bytes = algorithmic_bytes(A, r["flop_s"], r["n_sampled"])
     peak, peak_src = measured_peaks()
     achieved = kern_bytes / (t_kern * 1e-3) / 1e9
     traffic = profiled_traffic()
@@ -387,12 +386,13 @@ def run_ours(args):
         "hbm_gbs_call": call_bytes / (t_step * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_flop_pred<predict> (FLOP per row + prediction + scan)",
+                     "kernel": "k_predict<predict> (the whole call: B row-length table, sample, "
+                               "FLOP per row, heavy sampled rows, prediction, scan)",
                      "algorithmic_bytes": kern_bytes, "kernel_ms": t_kern, "peak_source": peak_src,
                      "l2_lookups_per_s": A.nnz / (t_kern * 1e-3)},
         "e2e": {"value": eu / es, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": E},
-        "gpu_launches": 3 * K,
+        "gpu_launches": K,
         "exact_symbolic": {"ms": t_sym, "input_nnz_per_s": A.nnz / (t_sym * 1e-3),
                            "prediction_speedup": t_sym / t_step, "Z": sr["pred_total"]},
         "accuracy": {"eps1": est["eps1"], "eps_f": est["eps_f"], "eps2": est["eps2"],

@@ -11,6 +11,7 @@
 #include "k_batch.cuh"
 #include "k_dedup.cuh"
 #include "k_flop.cuh"
+#include "k_predict.cuh"
 #include "k_scan.cuh"
 
 using namespace spg;
@@ -40,6 +41,9 @@ struct DeviceLimits {
   int kb_flop_blocks_per_sm = 0;
   int kb_heavy_dyn_smem = 0;
   int kb_heavy_bitmap_words = 0;
+  // single-launch predictor
+  int pred_blocks_per_sm = 0;
+  int pred_dyn_smem = 0;
   bool ok = false;
 };
 
@@ -100,7 +104,16 @@ void init_limits(int dev, DeviceLimits* L) {
   }
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kb_flop, kFlopThreads, 0) != cudaSuccess) return;
   L->kb_flop_blocks_per_sm = b;
-  L->ok = L->flop_blocks_per_sm > 0 && L->scan_blocks_per_sm > 0 && L->dedup_blocks_per_sm > 0 &&
+  // single-launch predictor: a fixed 128 KB of dynamic shared memory (the rest
+  // of the SM's 256 KB stays L1 for the FLOP pass)
+  const int pdyn = (int)kPredDynSmem;
+  if (cudaFuncSetAttribute(k_predict<kModePredict>, cudaFuncAttributeMaxDynamicSharedMemorySize, pdyn) != cudaSuccess) return;
+  if (cudaFuncSetAttribute(k_predict<kModeReference>, cudaFuncAttributeMaxDynamicSharedMemorySize, pdyn) != cudaSuccess) return;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_predict<kModePredict>, kPredThreads, pdyn) != cudaSuccess) return;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_predict<kModeReference>, kPredThreads, pdyn) != cudaSuccess) return;
+  L->pred_blocks_per_sm = min(b, b2);
+  L->pred_dyn_smem = pdyn;
+  L->ok = L->pred_blocks_per_sm > 0 && L->flop_blocks_per_sm > 0 && L->scan_blocks_per_sm > 0 && L->dedup_blocks_per_sm > 0 &&
           L->kb_flop_blocks_per_sm > 0 && L->kb_sample_blocks_per_sm[0] > 0 &&
           L->kb_sample_blocks_per_sm[1] > 0 && L->kb_sample_blocks_per_sm[2] > 0;
 }
@@ -244,6 +257,31 @@ int launch_scan(const DeviceLimits* L, const Src& src, long long n, const Worksp
   return cudaGetLastError() == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 
+// One cooperative launch of the single-launch predictor over the operands of
+// pa (all blocks co-resident).
+template <int MODE>
+int launch_predict(const DeviceLimits* L, const PredArgs& pa, cudaStream_t st) {
+  const long long D = pa.f.M + pa.f.nnzA;
+  long long g = (D + kPredItemsPerBlock - 1) / kPredItemsPerBlock;
+  const long long cap = std::min<long long>((long long)L->sms * L->pred_blocks_per_sm, kMaxSlots);
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)g);
+  lc.blockDim = dim3(kPredThreads);
+  lc.dynamicSmemBytes = (size_t)L->pred_dyn_smem;
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  prof_mark(false, st);
+  const cudaError_t e = cudaLaunchKernelEx(&lc, k_predict<MODE>, pa);
+  prof_mark(true, st);
+  return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
 int predict_common(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_config_t* cfg,
                    int32_t* pred_row, int64_t* offsets, int32_t* flop_row, spgemm_result_t* res,
                    void* ws, size_t ws_bytes, void* stream, bool reference) {
@@ -261,9 +299,12 @@ int predict_common(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_co
   d.seed = cfg->seed;
   d.threshold = cfg->threshold;
   d.n_cand = n_cand;
-  if ((rc = launch_dedup(L, d, st))) return rc;
-  FlopArgs f = flop_args(A, B, w, flop_row, pred_row, offsets, res, !reference);
-  return reference ? launch_flop<kModeReference>(L, f, st) : launch_flop<kModePredict>(L, f, st);
+  PredArgs pa;
+  pa.f = flop_args(A, B, w, flop_row, pred_row, offsets, res, false);
+  pa.d = d;
+  pa.bitmap_words = L->pred_dyn_smem / 4;
+  pa.flop_out = flop_row != nullptr;
+  return reference ? launch_predict<kModeReference>(L, pa, st) : launch_predict<kModePredict>(L, pa, st);
 }
 
 // ---- scratch for spgemm_predict_structure_static --------------------------------

@@ -32,8 +32,15 @@ struct alignas(128) WsHeader {
   unsigned int status;       // SPGEMM_STATUS_* bits (atomicOr)
   unsigned int epoch;        // flag epoch of the previous completed launch
   unsigned int done;         // blocks finished in the current launch
-  unsigned int pad[24];
+  // progress counters of the single-launch predictor (k_predict)
+  unsigned int table_done;   // blocks whose share of the B row-length table is written
+  unsigned int sample_done;  // blocks whose sampled rows are counted or queued
+  unsigned int heavy_ctr;    // heavy-queue entries claimed
+  unsigned int heavy_done;   // heavy rows counted
+  unsigned int stream_done;  // blocks whose FLOP pass is finished
+  unsigned int pad[19];
 };
+static_assert(sizeof(WsHeader) == 256, "workspace header layout");
 
 struct alignas(64) Slot {
   unsigned int carry_flag;  // = epoch when `carry` is valid
@@ -120,6 +127,22 @@ __device__ __forceinline__ int pred_proposed(uint32_t v, uint64_t z, uint64_t f,
   return (int)q;
 }
 
+// The same ceiling without floating point, for a whole launch's rows: R =
+// floor(z * 2^64 / f) is prepared once (pred_recip, for 0 < z < f); then
+// q = floor(v * R / 2^64) is floor(v * z / f) or one less, and the exact ceiling
+// is q, q + 1 or q + 2, decided by two 128-bit comparisons with v * z.
+__device__ __forceinline__ uint64_t pred_recip(uint64_t z, uint64_t f) {
+  return (uint64_t)(((u128)z << 64) / (u128)f);
+}
+__device__ __forceinline__ int pred_fixed(uint32_t v, uint64_t z, uint64_t f, uint64_t R) {
+  uint64_t q = __umul64hi((uint64_t)v, R);
+  const u128 num = (u128)v * z;
+  if ((u128)q * f >= num) return (int)q;
+  ++q;
+  if ((u128)q * f >= num) return (int)q;
+  return (int)(q + 1);
+}
+
 // ceil(v * zm / den) for the reference design: zm = z * M (< 2^94),
 // den = F * |S| (< 2^94).  Saturates at 2^31 - 1 and reports it via *sat.
 __device__ __forceinline__ int pred_reference(uint32_t v, u128 zm, u128 den, double ratio,
@@ -164,32 +187,65 @@ __device__ __forceinline__ T warp_incl_scan(T v) {
   return v;
 }
 
-// Block-wide exclusive scan of one value per thread; returns the exclusive
-// prefix and writes the block total to *total.  `sm` needs NW + 1 entries.
-template <int NT>
+// ---------------------------------------------------------------------------
+// Thread groups: the NT threads of warps [WOFF, WOFF + NT/32) of a block,
+// synchronised by hardware barrier BAR (0 = the whole block, __syncthreads).
+// Every thread of the group must reach each call.
+// ---------------------------------------------------------------------------
+template <int BAR, int NT>
+__device__ __forceinline__ void group_sync() {
+  if (BAR == 0) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(BAR), "r"(NT) : "memory");
+  }
+}
+
+// Number of threads of the group with p true (a barrier, like __syncthreads_count).
+template <int BAR, int NT>
+__device__ __forceinline__ int group_count(bool p) {
+  if (BAR == 0) return __syncthreads_count(p);
+  unsigned n;
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n bar.red.popc.u32 %0, %2, %3, q;\n}"
+      : "=r"(n)
+      : "r"((unsigned)p), "r"(BAR), "r"(NT)
+      : "memory");
+  return (int)n;
+}
+
+template <int BAR, int NT>
+__device__ __forceinline__ bool group_or(bool p) {
+  if (BAR == 0) return __syncthreads_or(p);
+  return group_count<BAR, NT>(p) != 0;
+}
+
+// Group-wide exclusive scan of one value per thread; returns the exclusive
+// prefix and writes the group total to *total.  `sm` needs NT/32 + 1 entries.
+template <int NT, int BAR = 0, int WOFF = 0>
 __device__ __forceinline__ long long block_excl_scan(long long v, long long* sm, long long* total) {
   constexpr int NW = NT / 32;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = (int)(threadIdx.x >> 5) - WOFF;
   long long inc = warp_incl_scan(v);
   if (lane == 31) sm[w] = inc;
-  __syncthreads();
+  group_sync<BAR, NT>();
   if (w == 0) {
     long long t = lane < NW ? sm[lane] : 0;
     long long ti = warp_incl_scan(t);
     if (lane < NW) sm[lane] = ti - t;
     if (lane == NW - 1) sm[NW] = ti;
   }
-  __syncthreads();
+  group_sync<BAR, NT>();
   long long r = sm[w] + inc - v;
   *total = sm[NW];
-  __syncthreads();
+  group_sync<BAR, NT>();
   return r;
 }
 
-template <int NT>
+template <int NT, int BAR = 0, int WOFF = 0>
 __device__ __forceinline__ long long block_sum(long long v, long long* sm) {
   long long t;
-  block_excl_scan<NT>(v, sm, &t);
+  block_excl_scan<NT, BAR, WOFF>(v, sm, &t);
   return t;
 }
 
@@ -227,17 +283,33 @@ __device__ __noinline__ bool flag_wait(const unsigned int* p, unsigned int want,
   return false;
 }
 
+// Waits until *p >= want (a counter that only grows within a launch); gives up
+// like flag_wait.
+__device__ __noinline__ bool count_wait(const unsigned int* p, unsigned int want, unsigned int* status) {
+  if (flag_load(p) >= want) return true;
+  const uint64_t t0 = global_ns();
+  unsigned ns = 32;
+  for (int it = 0; it < (1 << 26); ++it) {
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+    if (flag_load(p) >= want) return true;
+    if ((it & 63) == 63 && global_ns() - t0 > 1000000000ull) break;
+  }
+  atomicOr(status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);
+  return false;
+}
+
 __device__ __forceinline__ void set_status(WsHeader* h, unsigned bits) { atomicOr(&h->status, bits); }
 
 // Byte table of B's row lengths: deg8[k] = min(B.rpt[k+1] - B.rpt[k], kDegEscape).
 // Lookups into this 1-byte table replace the pair of B.rpt loads per nonzero
 // in the FLOP pass (fewer L2 sectors and more L1 reuse); kDegEscape means
-// "read B.rpt".  Offsets out of range give 0 and the bad-input status bit.
-__global__ void k_degree_table(const int* b_rpt, long long K, long long nnzB, unsigned char* deg8,
-                               WsHeader* hdr) {
-  bool bad = false;
-  const long long stride = (long long)gridDim.x * blockDim.x * 4;
-  for (long long k0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4; k0 < K; k0 += stride) {
+// "read B.rpt".  Offsets out of range give 0 and set *bad.  Thread `first` of
+// `nthreads` writes the 4-row words first, first + nthreads, ...
+__device__ __forceinline__ void degree_words(const int* b_rpt, long long K, long long nnzB,
+                                             unsigned char* deg8, long long first, long long nthreads,
+                                             bool& bad) {
+  for (long long k0 = first * 4; k0 < K; k0 += nthreads * 4) {
     unsigned word = 0;
     long long prev = __ldg(b_rpt + k0);
 #pragma unroll
@@ -255,6 +327,13 @@ __global__ void k_degree_table(const int* b_rpt, long long K, long long nnzB, un
     }
     *reinterpret_cast<unsigned*>(deg8 + k0) = word;
   }
+}
+
+__global__ void k_degree_table(const int* b_rpt, long long K, long long nnzB, unsigned char* deg8,
+                               WsHeader* hdr) {
+  bool bad = false;
+  degree_words(b_rpt, K, nnzB, deg8, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+               (long long)gridDim.x * blockDim.x, bad);
   if (bad) atomicOr(&hdr->status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
 }
 

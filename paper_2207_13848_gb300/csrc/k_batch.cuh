@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(kDedupThreads) kb_sample(BatchArgs b) {
     while (base < c_end) {
       if (t == 0) list_n = 0;
       __syncthreads();
+      int n = 0;  // rows staged: the same in every thread (the barrier's count)
       for (;;) {
         const long long x = base + t;
         bool take = false;
@@ -251,10 +252,9 @@ __global__ void __launch_bounds__(kDedupThreads) kb_sample(BatchArgs b) {
           list_case[e] = cx;
         }
         base += kDedupThreads;
-        __syncthreads();
-        if (base >= c_end || list_n > kListCap - kDedupThreads) break;
+        n += __syncthreads_count(take);
+        if (base >= c_end || n > kListCap - kDedupThreads) break;
       }
-      const int n = list_n;
       for (int e = warp; e < n; e += kDedupWarps) {
         const int c = list_case[e], r = list_row[e];
         if (c != cur) {
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kHeavyThreads) kb_heavy(BatchArgs b, int bitma
     __syncthreads();
     const unsigned h = s_h;
     if (h >= n_heavy) break;
-    const int g = b.heavy[h];
+    const int g = b.heavy[h] - 1;
     if (t < 32) {
       const int c = warp_last_le(b.n_cases, (long long)g, [&](int i) { return b.cases[i].row_base; });
       if (t == 0) {
@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(kHeavyThreads) kb_heavy(BatchArgs b, int bitma
       }
     }
     __syncthreads();
+    if (t == 0) b.heavy[h] = 0;  // taken: every thread has read the entry
     const int c = s_case;
     bool bad = false;
     const long long nnz = heavy_row_nnz(ha, g - ha.heavy_base, sm, tab, bitmap_words, bad);

@@ -42,7 +42,9 @@ struct DedupArgs {
   unsigned int* status;  // where SPGEMM_STATUS_* bits go (the header's, or a batch case's)
   // Rows with more than heavy_thr products (at most half the warp table) are
   // queued for the block-per-row pass: heavy[atomicAdd(heavy_count, 1)] =
-  // heavy_base + row, while fewer than heavy_cap entries are queued.
+  // heavy_base + row + 1, while fewer than heavy_cap entries are queued.  A
+  // queue entry of 0 is empty; whoever takes an entry sets it back to 0, so the
+  // queue is empty again after every call.
   unsigned int* heavy_count;
   int* heavy;
   long long heavy_cap;
@@ -183,7 +185,7 @@ __device__ long long dedup_row_warp(const DedupArgs& a, int row, int* tbl, long 
 
   if (lane == 0) {
     const unsigned h = atomicAdd(a.heavy_count, 1u);
-    if (h < (unsigned long long)a.heavy_cap) a.heavy[h] = a.heavy_base + row;
+    if (h < (unsigned long long)a.heavy_cap) flag_store(reinterpret_cast<unsigned*>(a.heavy + h), (unsigned)(a.heavy_base + row + 1));
   }
   return -1;
 }
@@ -206,7 +208,9 @@ __global__ void __launch_bounds__(kDedupThreads) k_dedup_rows(DedupArgs a) {
   while (base < c_end) {
     if (threadIdx.x == 0) list_n = 0;
     __syncthreads();
-    // stage selected rows until the list could overflow or the slice ends
+    // stage selected rows until the list could overflow or the slice ends; n
+    // (the same in every thread, from the barrier's count) is the number staged
+    int n = 0;
     for (;;) {
       const long long cand = base + threadIdx.x;
       bool take = false;
@@ -229,10 +233,9 @@ __global__ void __launch_bounds__(kDedupThreads) k_dedup_rows(DedupArgs a) {
       wbase = __shfl_sync(kFull, wbase, 0);
       if (take) list[wbase + __popc(bal & ((1u << lane) - 1u))] = row;
       base += kDedupThreads;
-      __syncthreads();
-      if (base >= c_end || list_n > kListCap - kDedupThreads) break;
+      n += __syncthreads_count(take);
+      if (base >= c_end || n > kListCap - kDedupThreads) break;
     }
-    const int n = list_n;
     for (int e = warp; e < n; e += kDedupWarps) {
       const int r = list[e];
       long long flop;
@@ -323,7 +326,7 @@ __device__ long long heavy_count_pass(const DedupArgs& a, long long rb, long lon
 // shared hash table when the row has at most kBlockHashCap products, else a
 // bitmap over B's columns, one column range of bitmap_words * 32 at a time.
 __device__ long long heavy_row_nnz(const DedupArgs& a, int row, HeavySmem& sm, unsigned* tab,
-                                   int bitmap_words, bool& bad) {
+                                   int bitmap_words, bool& bad, long long* flop_out = nullptr) {
   long long rb = __ldg(a.a_rpt + row), re = __ldg(a.a_rpt + row + 1);
   if (!clamp_range(rb, re, a.nnzA)) bad = true;
   // the row's FLOP decides the method
@@ -334,6 +337,7 @@ __device__ long long heavy_row_nnz(const DedupArgs& a, int row, HeavySmem& sm, u
     fl += len;
   }
   const long long flop = block_sum<kHeavyThreads>(fl, sm.red);
+  if (flop_out) *flop_out = flop;
   long long nnz = 0;
   if (flop <= kBlockHashCap) {
     const int lg = ceil_log2((uint32_t)(2 * flop));
@@ -358,7 +362,9 @@ __global__ void __launch_bounds__(kHeavyThreads) k_dedup_heavy(DedupArgs a, int 
   __shared__ HeavySmem sm;
   const unsigned n_heavy = (unsigned)min((long long)*a.heavy_count, a.heavy_cap);
   for (unsigned h = blockIdx.x; h < n_heavy; h += gridDim.x) {
-    const int row = a.heavy[h];
+    const int row = a.heavy[h] - 1;
+    __syncthreads();
+    if (threadIdx.x == 0) a.heavy[h] = 0;
     bool bad = false;
     const long long nnz = heavy_row_nnz(a, row, sm, tab, bitmap_words, bad);
     if (threadIdx.x == 0) {

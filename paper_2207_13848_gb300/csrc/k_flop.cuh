@@ -113,40 +113,58 @@ struct RangeOut {
   bool head_pending;           // the first row waits for the previous range's carry
 };
 
-struct FlopShared {
-  alignas(16) int lens[kFlopWarps][kSub];  // prefix sums of B row lengths over a warp's step
-  WarpInfo info[kFlopWarps];
-  long long red[kFlopWarps + 1];
+template <int NW>
+struct FlopSharedT {
+  alignas(16) int lens[NW][kSub];  // prefix sums of B row lengths over a warp's step
+  WarpInfo info[NW];
+  long long red[NW + 1];
   long long bc[8];
   RangeOut out;
 };
+using FlopShared = FlopSharedT<kFlopWarps>;
 
-// One block streams the items [d0, d1) of the merged sequence: every row that
+// B row-length table lookup.  A plain (coherent) load: the fused predictor
+// builds the table earlier in the same launch, so the read-only path is not
+// used for it.
+__device__ __forceinline__ unsigned table_load(const unsigned char* p) { return *p; }
+
+// One block (or the group of NW warps starting at warp WOFF, synchronised by
+// hardware barrier BAR) streams the items [d0, d1) of the merged sequence: every row that
 // ends in the range and starts in it gets its prediction (predict mode) or its
 // FLOP written; rows split between warps are joined here; the row split with
 // the previous range (has_prev) and the row left open at the end are reported
-// in *out (written by thread 0; all threads may read it on return).  ftot/ptot
+// in *out (written by the group's first thread; all its threads may read it on
+// return).  ftot/ptot
 // receive this thread's share of the FLOP / prediction sums of finished rows.
-template <int MODE>
+template <int MODE, int NW, int WOFF = 0, int BAR = 0>
 __device__ __forceinline__ void flop_range(const FlopArgs& a, long long d0, long long d1, bool has_prev,
                                            unsigned long long fz, unsigned long long zz, double ratio,
-                                           FlopShared& sm, RangeOut* out, long long& ftot,
-                                           long long& ptot, bool& bad) {
+                                           FlopSharedT<NW>& sm, RangeOut* out, long long& ftot,
+                                           long long& ptot, bool& bad, int* sflop = nullptr,
+                                           int sflop_n = 0, bool flop_global = true) {
   // ---- the range is split evenly among the block's warps; each warp finds
   // both of its bounds in one pass, and the range's bounds are the first
   // warp's start and the last warp's end
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int t = threadIdx.x, lane = t & 31, warp = (t >> 5) - WOFF;
+  const bool leader = t == WOFF * 32;
   const int K = (int)a.K;
   const int M = (int)a.M;
-  const long long wd0 = d0 + (d1 - d0) * warp / kFlopWarps;
-  const long long wd1 = d0 + (d1 - d0) * (warp + 1) / kFlopWarps;
+  const long long wd0 = d0 + (d1 - d0) * warp / NW;
+  const long long wd1 = d0 + (d1 - d0) * (warp + 1) / NW;
   long long wl0, wl1;
   merge_path_rows2(a.a_rpt, a.M, wd0, wd1, &wl0, &wl1);
   if (lane == 0 && warp == 0) sm.bc[0] = wl0;
-  if (lane == 0 && warp == kFlopWarps - 1) sm.bc[1] = wl1;
-  __syncthreads();
+  if (lane == 0 && warp == NW - 1) sm.bc[1] = wl1;
+  group_sync<BAR, NW * 32>();
   const long long bi0 = sm.bc[0], bi1 = sm.bc[1];
   const int i0 = (int)bi0, i1 = (int)bi1;
+  // FLOP mode: the block's row r goes to sflop[r - i0] when it fits there, and
+  // to a.flop[r] when flop_global or when it does not fit
+  auto store_flop = [&](int r, int v) {
+    const bool in_s = sflop != nullptr && (unsigned)(r - i0) < (unsigned)sflop_n;
+    if (in_s) sflop[r - i0] = v;
+    if (flop_global || !in_s) a.flop[r] = v;
+  };
   const int j0 = (int)min(max(d0 - bi0, 0ll), (long long)a.nnzA);
   const int j1 = (int)max(min(max(d1 - bi1, 0ll), (long long)a.nnzA), (long long)j0);
   const int wi0 = (int)wl0, wi1 = (int)wl1;
@@ -198,7 +216,7 @@ __device__ __forceinline__ void flop_range(const FlopArgs& a, long long d0, long
           ptot += p;
           if (a.flop) a.flop[r] = v;
         } else {
-          a.flop[r] = v;
+          store_flop(r, v);
         }
       }
     }
@@ -245,7 +263,7 @@ __device__ __forceinline__ void flop_range(const FlopArgs& a, long long d0, long
       len[u] = 0;
       if (q >= lo && q < hi) {
         if ((unsigned)cc < (unsigned)K) {
-          len[u] = __ldg(a.deg8 + cc);
+          len[u] = table_load(a.deg8 + cc);
         } else {
           bad = true;
         }
@@ -311,17 +329,17 @@ __device__ __forceinline__ void flop_range(const FlopArgs& a, long long d0, long
     w.tail_part = tail_part;
   }
   const bool blk_head_split = (i0 < M) && has_prev && (__ldg(a.a_rpt + i0) < j0);
-  __syncthreads();
+  group_sync<BAR, NW * 32>();
 
   // ---- rows split between warps (thread 0).  Only the range's first row can
   // depend on the carry from the previous range.
-  if (t == 0) {
+  if (leader) {
     long long run = 0;          // partial of the open row entering warp w
     bool dep = blk_head_split;  // ... plus the previous block's carry
     long long head_known = 0;   // block's first row: everything but the carry
     bool head_pending = false;
     long long extra_f = 0, extra_p = 0;
-    for (int w = 0; w < kFlopWarps; ++w) {
+    for (int w = 0; w < NW; ++w) {
       const WarpInfo& in = sm.info[w];
       if (!in.has_end) {
         run += in.tail_part;
@@ -340,7 +358,7 @@ __device__ __forceinline__ void flop_range(const FlopArgs& a, long long d0, long
             if (a.flop) a.flop[in.first_row] = (int)v;
             extra_p += p;
           } else {
-            a.flop[in.first_row] = (int)v;
+            store_flop(in.first_row, (int)v);
           }
         }
       }
@@ -357,7 +375,7 @@ __device__ __forceinline__ void flop_range(const FlopArgs& a, long long d0, long
     out->dep = dep;
     out->head_pending = head_pending;
   }
-  __syncthreads();
+  group_sync<BAR, NW * 32>();
 }
 
 template <int MODE>

@@ -1,0 +1,672 @@
+// The structure prediction of one product C = A * B as ONE persistent launch:
+// the proposed method (Eq. 4, Algorithm 2) or the reference design of the
+// prior sampling method (Eq. 2), from the sample to the allocation offsets.
+//
+// One 1024-thread block per SM; blocks meet only through counters and flags in
+// the workspace (all blocks are co-resident: the launch is cooperative and the
+// grid never exceeds what the device holds at once; every wait gives up after
+// about a second and reports SPGEMM_STATUS_ERR_TIMEOUT instead of hanging).
+// Each block runs two warp groups side by side, each on its own hardware
+// barrier, then the whole block finishes:
+//   sampling group (the first kSampWarps warps): the block's slice of the sample candidates
+//     (Sec. IV-A); FLOP and exact nnz of the sampled rows (Sec. IV-B; the hash
+//     loop of Algorithm 2).  The rows are counted together, stage by stage, so
+//     a batch of rows waits for each memory round trip once: their A offsets,
+//     the B ranges of all their entries, then all their products,
+//     deduplicated as (row, column) keys in one shared-memory table.  Rows too
+//     long for a batch are queued as heavy;
+//   streaming group (the other warps): its share of the B row-length byte table
+//     (see degree_words), then, once every block's share exists, the FLOP of
+//     every row of the block's merge-path range (Algorithm 1);
+//   whole block: the heavy sampled rows, taken from the queue one at a time,
+//     each counted by the whole block (hash table or column bitmap in shared
+//     memory); then, once f*, z* (and, for the reference design, F) are final,
+//     the per-row prediction of the block's rows, the sum of the totals of the
+//     blocks before it, and the exclusive scan into the offsets.
+// The sampling work is latency-bound and the FLOP pass is bound by the rate
+// of scattered table lookups, so the two groups overlap well; the per-row
+// FLOP stays in shared memory until the prediction.  The dynamic shared memory
+// is held to 128 KB so that the FLOP pass keeps a large L1.
+#pragma once
+
+#include "common.cuh"
+#include "k_dedup.cuh"
+#include "k_flop.cuh"
+
+namespace spg {
+
+constexpr int kPredThreads = 1024;
+constexpr int kPredWarps = kPredThreads / 32;
+constexpr long long kPredItemsPerBlock = 16384;  // merged items per block, at least
+static_assert(kPredThreads == kHeavyThreads, "heavy rows are counted by the whole block");
+
+// ---- the two warp groups --------------------------------------------------------
+#ifndef SPG_SAMP_WARPS
+#define SPG_SAMP_WARPS 12  // measured best on GB300 among 8, 12, 16 (ER n = 2^20)
+#endif
+constexpr int kSampWarps = SPG_SAMP_WARPS;
+constexpr int kSampThreads = kSampWarps * 32;
+constexpr int kStreamWarps = kPredWarps - kSampWarps;
+constexpr int kStreamThreads = kStreamWarps * 32;
+constexpr int kBarSamp = 1;    // hardware barrier of the sampling group
+constexpr int kBarStream = 2;  // hardware barrier of the streaming group
+
+// ---- sampling group: batch limits ------------------------------------------------
+constexpr int kSRows = kSampThreads;            // sampled rows per row round (one per thread)
+constexpr int kSEntPer = 4;                     // A entries per thread per entry round
+constexpr int kSEnts = kSampThreads * kSEntPer;  // A entries per entry round
+constexpr int kSEntMax = 256;                   // rows with more entries are queued as heavy
+constexpr int kSEntRound = kSEnts - kSEntMax;   // entry offsets at which entry rounds start
+constexpr int kSLgSlots = 13;                   // (row, column) table of 2^13 slots
+constexpr int kSSlots = 1 << kSLgSlots;
+constexpr int kSProdMax = 1024;                 // rows with more products are queued as heavy
+constexpr int kSProdRound = kSSlots / 2 - kSProdMax;  // product offsets at which rounds start
+constexpr int kSUnroll = 8;                     // products per thread loaded at once
+// product rounds of one entry round: at most kSRows rows of at most kSProdMax each
+constexpr int kSMaxRounds = kSRows * kSProdMax / kSProdRound + 2;
+constexpr int kSRowBits = kSRows <= 256 ? 8 : kSRows <= 512 ? 9 : 10;
+constexpr int kSColBits = 32 - kSRowBits;       // key = row << kSColBits | column: needs N < 2^kSColBits
+static_assert(kSRows <= (1 << kSRowBits), "row index fits the key");
+static_assert(kSMaxRounds <= kSampThreads, "one round start per thread");
+
+struct SampleSmem {
+  unsigned long long r_flop[kSRows];  // FLOP of each staged row (entry round)
+  int r_row[kSRows];                  // A row id of each staged row
+  int r_rb[kSRows];                   // its first entry in A
+  int r_eoff[kSRows];                 // exclusive prefix of the entries counted here
+  int e_bs[kSEnts];                   // B row start of each entry of the round
+  int e_bl[kSEnts];                   // B row length (0 once the row is queued as heavy)
+  int e_poff[kSEnts];                 // exclusive prefix of e_bl
+  int e_row[kSEnts];                  // staged row of each entry
+  int p_start[kSMaxRounds + 1];       // first product of each product round
+  int m_max;                          // last product round
+  int tbl[kSSlots];                   // (row, column) keys, -1 = empty
+};
+
+// ---- dynamic shared memory ------------------------------------------------------
+// [0, kOffFlopSm): the sampling group's batch (or its per-warp tables);
+// [kOffFlopSm, kOffSflop): the streaming group's buffers; [kOffSflop, end): the
+// FLOP of the block's first kSFlopN rows, kept until the prediction.  The
+// heavy rows then use the whole space (after the FLOP is copied out).
+constexpr size_t kPredDynSmem = 128 * 1024;
+constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kOffFlopSm = round256(sizeof(SampleSmem) > (size_t)kSampWarps * kWarpTable * sizeof(int)
+                                           ? sizeof(SampleSmem)
+                                           : (size_t)kSampWarps * kWarpTable * sizeof(int));
+constexpr size_t kOffSflop = kOffFlopSm + round256(sizeof(FlopSharedT<kStreamWarps>));
+constexpr int kSFlopN = (int)((kPredDynSmem - kOffSflop) / sizeof(int));
+static_assert(kOffSflop < kPredDynSmem, "groups' buffers fit");
+static_assert((size_t)kBlockHashSlots * sizeof(int) <= kPredDynSmem, "heavy-row hash fits");
+
+struct PredArgs {
+  FlopArgs f;        // rows, operands, FLOP buffer, outputs, workspace, result
+  DedupArgs d;       // the sample and the deduplication of its rows
+  int bitmap_words;  // 32-bit words of dynamic shared memory (heavy rows' bitmap)
+  int flop_out;      // f.flop is the caller's flop_row (else the workspace buffer)
+};
+
+constexpr int kListCapW = 1024;  // staged rows of the per-warp fallback
+
+struct PredStatic {
+  long long red[kPredWarps + 1];     // whole-block scans
+  long long red_s[kSampWarps + 1];   // sampling-group scans
+  long long bc[8];
+  int s_enc;
+  int list[kListCapW];
+  HeavySmem heavy;
+};
+
+// Candidate x of the sample: is it drawn, and which row (Sec. IV-A)?
+__device__ __forceinline__ bool sample_candidate(const DedupArgs& d, long long x, int* row) {
+  const uint32_t h = sample_hash32(d.seed, (uint64_t)x);
+  if (d.src == kSrcBernoulli) {
+    *row = (int)x;
+    return (uint64_t)h < d.threshold;
+  }
+  *row = (int)(((uint64_t)h * (uint64_t)d.M) >> 32);
+  return true;
+}
+
+// Queues a sampled row for the block-per-row pass.  The entry is row + 1 when
+// its FLOP is already counted, -(row + 1) when the pass must count it too.
+__device__ __forceinline__ void push_heavy(const DedupArgs& d, int row, bool flop_counted) {
+  const unsigned h = atomicAdd(d.heavy_count, 1u);
+  if (h < (unsigned long long)d.heavy_cap)
+    flag_store(reinterpret_cast<unsigned*>(d.heavy + h), flop_counted ? (unsigned)(row + 1) : (unsigned)(-(row + 1)));
+}
+
+// Index of the last i in [lo, hi) with v[i] <= x (v non-decreasing, v[lo] <= x).
+__device__ __forceinline__ int last_le(const int* v, int lo, int hi, long long x) {
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Sampling group, batched (B has fewer than 2^24 columns).  Adds this thread's
+// share of f*, z* and |S| to f_loc, z_loc, s_loc.
+__device__ void sample_batched(const DedupArgs& d, SampleSmem& sh, long long* red, long long& f_loc,
+                               long long& z_loc, long long& s_loc, bool& bad) {
+  constexpr int NT = kSampThreads;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int G = gridDim.x, c = blockIdx.x;
+  const long long c_beg = (long long)c * d.n_cand / G, c_end = (long long)(c + 1) * d.n_cand / G;
+  // thread t hashes the candidates [x0, x1) of the block's slice
+  const long long q = (c_end - c_beg + NT - 1) / NT;
+  const long long x0 = min(c_end, c_beg + t * q), x1 = min(c_end, x0 + q);
+  int cnt = 0;
+  for (long long x = x0; x < x1; ++x) {
+    int row;
+    cnt += sample_candidate(d, x, &row);
+  }
+  long long total;
+  const long long pre = block_excl_scan<NT, kBarSamp>(cnt, red, &total);
+  if (t == 0) s_loc += total;
+
+  for (long long R0 = 0; R0 < total; R0 += kSRows) {
+    // ---- the round's rows: sample indices [R0, R0 + nr), in candidate order
+    const int nr = (int)min((long long)kSRows, total - R0);
+    if (pre + cnt > R0 && pre < R0 + nr) {
+      long long idx = pre;
+      for (long long x = x0; x < x1 && idx < R0 + nr; ++x) {
+        int row;
+        if (sample_candidate(d, x, &row)) {
+          if (idx >= R0) sh.r_row[idx - R0] = row;
+          ++idx;
+        }
+      }
+    }
+    group_sync<kBarSamp, NT>();
+    // ---- stage 1: A offsets of every staged row (thread t: row t)
+    int nent = 0;
+    if (t < nr) {
+      const int row = sh.r_row[t];
+      long long rb = __ldg(d.a_rpt + row), re = __ldg(d.a_rpt + row + 1);
+      if (!clamp_range(rb, re, d.nnzA)) bad = true;
+      if (re - rb > kSEntMax) {
+        push_heavy(d, row, false);
+      } else {
+        nent = (int)(re - rb);
+      }
+      sh.r_rb[t] = (int)rb;
+    }
+    long long E;
+    const int eoff = (int)block_excl_scan<NT, kBarSamp>(nent, red, &E);
+    if (t < nr) sh.r_eoff[t] = eoff;
+    group_sync<kBarSamp, NT>();
+
+    // ---- entry rounds: rows whose entries start in [E0, E0 + kSEntRound)
+    for (long long E0 = 0; E0 < E; E0 += kSEntRound) {
+      const int ia = group_count<kBarSamp, NT>(t < nr && eoff < E0);
+      const int ib = group_count<kBarSamp, NT>(t < nr && eoff < E0 + kSEntRound);
+      const int ea = ia < nr ? sh.r_eoff[ia] : (int)E;
+      const int eb = ib < nr ? sh.r_eoff[ib] : (int)E;
+      const int ne = eb - ea;  // <= kSEnts
+      if (t >= ia && t < ib) sh.r_flop[t] = 0;
+      group_sync<kBarSamp, NT>();
+      // ---- stage 2: B range of every entry of the round (kSEntPer per thread,
+      // every load of a stage in flight together)
+      {
+        int ii[kSEntPer], kk[kSEntPer];
+#pragma unroll
+        for (int u = 0; u < kSEntPer; ++u) {
+          const int le = t + u * NT;
+          ii[u] = 0;
+          kk[u] = 0;
+          if (le < ne) {
+            const int g = ea + le;
+            ii[u] = last_le(sh.r_eoff, ia, ib, g);
+            kk[u] = __ldg(d.a_col + sh.r_rb[ii[u]] + (g - sh.r_eoff[ii[u]]));
+          }
+        }
+        int b0[kSEntPer], b1[kSEntPer];
+#pragma unroll
+        for (int u = 0; u < kSEntPer; ++u) {
+          b0[u] = 0;
+          b1[u] = 0;
+          if (t + u * NT < ne) {
+            if ((unsigned)kk[u] < (unsigned long long)d.K) {
+              b0[u] = __ldg(d.b_rpt + kk[u]);
+              b1[u] = __ldg(d.b_rpt + kk[u] + 1);
+            } else {
+              bad = true;
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kSEntPer; ++u) {
+          const int le = t + u * NT;
+          if (le < ne) {
+            long long lo = b0[u], hi = b1[u];
+            if (!clamp_range(lo, hi, d.nnzB)) bad = true;
+            sh.e_bs[le] = (int)lo;
+            sh.e_bl[le] = (int)(hi - lo);
+            sh.e_row[le] = ii[u];
+            atomicAdd(&sh.r_flop[ii[u]], (unsigned long long)(hi - lo));
+          }
+        }
+      }
+      group_sync<kBarSamp, NT>();
+      // rows with too many products go to the heavy queue (their FLOP counted here)
+      if (t >= ia && t < ib) {
+        const unsigned long long fl = sh.r_flop[t];
+        f_loc += (long long)fl;
+        if (fl > (unsigned long long)kSProdMax) {
+          push_heavy(d, sh.r_row[t], true);
+          sh.r_flop[t] = ~0ull;
+        }
+      }
+      group_sync<kBarSamp, NT>();
+      // products of each entry: exclusive prefix over the round's entries
+      int bl[kSEntPer];
+      int bsum = 0;
+#pragma unroll
+      for (int u = 0; u < kSEntPer; ++u) {
+        const int le = t * kSEntPer + u;
+        bl[u] = (le < ne && sh.r_flop[sh.e_row[le]] != ~0ull) ? sh.e_bl[le] : 0;
+        bsum += bl[u];
+      }
+      long long P;
+      int po = (int)block_excl_scan<NT, kBarSamp>(bsum, red, &P);
+#pragma unroll
+      for (int u = 0; u < kSEntPer; ++u) {
+        const int le = t * kSEntPer + u;
+        if (le < ne) {
+          sh.e_poff[le] = po;
+          sh.e_bl[le] = bl[u];
+        }
+        po += bl[u];
+      }
+      if (t <= kSMaxRounds) sh.p_start[t] = 0x7fffffff;
+      if (t == 0) sh.m_max = -1;
+      group_sync<kBarSamp, NT>();
+      // product rounds: round m holds the rows whose products start in
+      // [m * kSProdRound, (m + 1) * kSProdRound), so at most kSProdRound +
+      // kSProdMax products, half the table's slots.  Consecutive rows start at
+      // most kSProdMax < kSProdRound products apart, so rounds 0..m_max all hold
+      // a row; round m's products are [p_start[m], p_start[m + 1]) (P for the last).
+      if (t >= ia && t < ib) {
+        const unsigned long long fl = sh.r_flop[t];
+        if (fl != ~0ull && fl > 0) {
+          const int st = sh.e_poff[sh.r_eoff[t] - ea];
+          const int m = st / kSProdRound;
+          atomicMin(&sh.p_start[m], st);
+          atomicMax(&sh.m_max, m);
+        }
+      }
+      group_sync<kBarSamp, NT>();
+      const int nrounds = sh.m_max + 1;
+      for (int m = 0; m < nrounds; ++m) {
+        const int pa = sh.p_start[m], pb = m + 1 < nrounds ? sh.p_start[m + 1] : (int)P;
+        for (int i = t; i < kSSlots; i += NT) sh.tbl[i] = -1;
+        group_sync<kBarSamp, NT>();
+        // warp w takes a contiguous run of U * 32 products, lanes interleaved;
+        // a lane loads kSUnroll column ids before inserting them
+        const int U = (pb - pa + NT - 1) / NT;
+        const int w0 = pa + warp * U * 32, w1 = min(pb, w0 + U * 32);
+        int e = w0 + lane < w1 ? last_le(sh.e_poff, 0, ne, w0 + lane) : 0;
+        for (int kb = 0; kb < U; kb += kSUnroll) {
+          unsigned key_hi[kSUnroll];
+          int col[kSUnroll];
+#pragma unroll
+          for (int k = 0; k < kSUnroll; ++k) {
+            const int pk = w0 + lane + 32 * (kb + k);
+            key_hi[k] = 0xffffffffu;
+            col[k] = 0;
+            if (kb + k < U && pk < w1) {
+              while (e + 1 < ne && sh.e_poff[e + 1] <= pk) ++e;
+              key_hi[k] = (unsigned)sh.e_row[e] << kSColBits;
+              col[k] = __ldg(d.b_col + sh.e_bs[e] + (pk - sh.e_poff[e]));
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < kSUnroll; ++k) {
+            if (key_hi[k] != 0xffffffffu) {
+              if ((unsigned)col[k] < (unsigned long long)d.N) {
+                z_loc += table_insert(sh.tbl, kSLgSlots, (int)(key_hi[k] | (unsigned)col[k]));
+              } else {
+                bad = true;
+              }
+            }
+          }
+        }
+        group_sync<kBarSamp, NT>();
+      }
+    }
+    group_sync<kBarSamp, NT>();
+  }
+}
+
+// Sampling group for B with 2^24 columns or more: each warp counts its rows
+// alone (dedup_row_warp), with a table of kWarpTable slots per warp.
+__device__ void sample_per_warp(const DedupArgs& d, int* tables, int* list, long long* red, long long& f_loc,
+                                long long& z_loc, long long& s_loc) {
+  constexpr int NT = kSampThreads;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int G = gridDim.x, c = blockIdx.x;
+  int* tbl = tables + warp * kWarpTable;
+  const long long c_beg = (long long)c * d.n_cand / G, c_end = (long long)(c + 1) * d.n_cand / G;
+  long long base = c_beg;
+  while (base < c_end) {
+    // stage selected rows until the list could overflow or the slice ends; n
+    // (the same in every thread) is the number staged so far
+    int n = 0;
+    for (;;) {
+      const long long cand = base + t;
+      int row = 0;
+      const bool take = cand < c_end && sample_candidate(d, cand, &row);
+      const unsigned bal = __ballot_sync(kFull, take);
+      if (lane == 0) red[warp] = __popc(bal);
+      group_sync<kBarSamp, NT>();
+      int wbase = n;
+      for (int w = 0; w < warp; ++w) wbase += (int)red[w];
+      if (take) list[wbase + __popc(bal & ((1u << lane) - 1u))] = row;
+      base += NT;
+      n += group_count<kBarSamp, NT>(take);
+      if (base >= c_end || n > kListCapW - NT) break;
+    }
+    for (int e = warp; e < n; e += kSampWarps) {
+      long long flop;
+      const long long nnz = dedup_row_warp(d, list[e], tbl, &flop);
+      if (lane == 0) {
+        f_loc += flop;
+        s_loc += 1;
+        if (nnz >= 0) z_loc += nnz;
+      }
+    }
+    group_sync<kBarSamp, NT>();
+  }
+}
+
+// Thread 0: claims the next heavy-queue entry and returns it (see push_heavy),
+// or 0 once every queued row is taken (the queue is final when every block's
+// sampling group has finished).  Waits for an entry whose writer has not
+// stored it yet.
+__device__ int claim_heavy_row(WsHeader* hdr, int* heavy, unsigned long long cap, unsigned G) {
+  const unsigned h = atomicAdd(&hdr->heavy_ctr, 1u);
+  const uint64_t t0 = global_ns();
+  unsigned ns = 32;
+  for (int it = 0; it < (1 << 26); ++it) {
+    if (h < cap) {
+      const unsigned v = flag_load(reinterpret_cast<const unsigned*>(heavy + h));
+      if (v != 0) {
+        heavy[h] = 0;  // taken
+        return (int)v;
+      }
+    }
+    if (flag_load(&hdr->sample_done) >= G) {
+      const unsigned long long n = min((unsigned long long)flag_load(&hdr->heavy_count), cap);
+      if (h >= n) return 0;  // the entry exists otherwise; its store is on its way
+    }
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+    if ((it & 63) == 63 && global_ns() - t0 > 1000000000ull) break;
+  }
+  atomicOr(&hdr->status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);
+  return 0;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
+  static_assert(MODE == kModePredict || MODE == kModeReference, "prediction modes only");
+  extern __shared__ __align__(16) unsigned char pdyn[];
+  __shared__ PredStatic ss;
+  const FlopArgs& a = p.f;
+  const DedupArgs& d = p.d;
+  const int t = threadIdx.x;
+  const int G = gridDim.x, c = blockIdx.x;
+  WsHeader* hdr = a.ws.hdr;
+  Slot* slots = a.ws.slots;
+  const unsigned ep = *reinterpret_cast<volatile unsigned*>(&hdr->epoch) + 1u;
+  const int M = (int)a.M;
+  int* sflop = reinterpret_cast<int*>(pdyn + kOffSflop);
+  FlopSharedT<kStreamWarps>& fs = *reinterpret_cast<FlopSharedT<kStreamWarps>*>(pdyn + kOffFlopSm);
+  long long ftot = 0;  // streaming threads: FLOP of the finished rows they wrote
+
+  if (t < kSampThreads) {
+    // ---- sampling group: this block's slice of the sample candidates
+    long long f_loc = 0, z_loc = 0, s_loc = 0;
+    bool bad = false;
+    if (d.N < (1ll << kSColBits)) {
+      sample_batched(d, *reinterpret_cast<SampleSmem*>(pdyn), ss.red_s, f_loc, z_loc, s_loc, bad);
+    } else {
+      sample_per_warp(d, reinterpret_cast<int*>(pdyn), ss.list, ss.red_s, f_loc, z_loc, s_loc);
+    }
+    if (group_or<kBarSamp, kSampThreads>(bad) && t == 0) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
+    const long long f = block_sum<kSampThreads, kBarSamp>(f_loc, ss.red_s);
+    const long long z = block_sum<kSampThreads, kBarSamp>(z_loc, ss.red_s);
+    const long long s = block_sum<kSampThreads, kBarSamp>(s_loc, ss.red_s);
+    if (t == 0) {
+      if (f) atomicAdd(&hdr->f_acc, (unsigned long long)f);
+      if (z) atomicAdd(&hdr->z_acc, (unsigned long long)z);
+      if (s) atomicAdd(&hdr->s_acc, (unsigned long long)s);
+      __threadfence();
+      atomicAdd(&hdr->sample_done, 1u);
+    }
+  } else {
+    // ---- streaming group: the table share, then the FLOP of the block's rows
+    constexpr int L = kSampThreads;  // the group's first thread
+    bool bad = false;
+    degree_words(a.b_rpt, a.K, a.nnzB, a.ws.deg8, (long long)c * kStreamThreads + (t - L),
+                 (long long)G * kStreamThreads, bad);
+    if (group_or<kBarStream, kStreamThreads>(bad) && t == L) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
+    if (t == L) {
+      __threadfence();
+      atomicAdd(&hdr->table_done, 1u);
+      count_wait(&hdr->table_done, (unsigned)G, &hdr->status);
+    }
+    group_sync<kBarStream, kStreamThreads>();
+    const long long D = a.M + a.nnzA;
+    const long long d0 = (long long)c * D / G, d1 = (long long)(c + 1) * D / G;
+    bad = false;
+    long long ptot = 0;
+    flop_range<kModeFlop, kStreamWarps, kSampWarps, kBarStream>(a, d0, d1, c > 0, 0ull, 0ull, 0.0, fs, &fs.out,
+                                                                ftot, ptot, bad, sflop, kSFlopN,
+                                                                p.flop_out != 0);
+    if (group_or<kBarStream, kStreamThreads>(bad) && t == L) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
+    if (t == L) {
+      const long long run = fs.out.run;
+      const int i0 = fs.out.i0, i1 = fs.out.i1;
+      long long extra_f = fs.out.extra_f;
+      // the FLOP of a row that spans blocks (waits only on block c - 1)
+      if (fs.out.dep) {
+        long long cin = 0;
+        if (flag_wait(&slots[c - 1].carry_flag, ep, &hdr->status)) cin = slots[c - 1].carry;
+        slots[c].carry = cin + run;
+        flag_store(&slots[c].carry_flag, ep);
+      } else {
+        slots[c].carry = i1 < M ? run : 0;
+        flag_store(&slots[c].carry_flag, ep);
+        if (fs.out.head_pending) {
+          long long cin = 0;
+          if (flag_wait(&slots[c - 1].carry_flag, ep, &hdr->status)) cin = slots[c - 1].carry;
+          const long long v = cin + fs.out.head_known;
+          sflop[0] = (int)v;
+          if (p.flop_out) a.flop[i0] = (int)v;
+          extra_f += v;
+        }
+      }
+      ss.bc[4] = extra_f;
+      ss.bc[6] = i0;
+      ss.bc[7] = i1;
+    }
+  }
+  __syncthreads();
+
+  // ---- the block's FLOP total
+  const int i0 = (int)ss.bc[6], i1 = (int)ss.bc[7];
+  {
+    const long long blk_f = block_sum<kPredThreads>(ftot, ss.red) + ss.bc[4];
+    if (t == 0) {
+      atomicAdd(&hdr->F_acc, (unsigned long long)blk_f);
+      __threadfence();
+      atomicAdd(&hdr->stream_done, 1u);
+    }
+  }
+
+  // ---- heavy sampled rows, one at a time, by the whole block
+  bool flop_in_smem = true;  // the FLOP of rows [i0, i0 + kSFlopN) is in sflop
+  {
+    unsigned* tab = reinterpret_cast<unsigned*>(pdyn);
+    for (;;) {
+      if (t == 0) ss.s_enc = claim_heavy_row(hdr, d.heavy, (unsigned long long)d.heavy_cap, (unsigned)G);
+      __syncthreads();
+      const int enc = ss.s_enc;
+      if (enc == 0) break;
+      if (flop_in_smem) {  // the table below overwrites sflop: move it to f.flop first
+        if (!p.flop_out)
+          for (int r = i0 + t; r < min(i1, i0 + kSFlopN); r += kPredThreads) a.flop[r] = sflop[r - i0];
+        flop_in_smem = false;
+        __syncthreads();
+      }
+      const int row = enc > 0 ? enc - 1 : -enc - 1;
+      bool bad = false;
+      long long flop = 0;
+      const long long nnz = heavy_row_nnz(d, row, ss.heavy, tab, p.bitmap_words, bad, &flop);
+      if (t == 0) {
+        atomicAdd(&hdr->z_acc, (unsigned long long)nnz);
+        if (enc < 0) atomicAdd(&hdr->f_acc, (unsigned long long)flop);
+        __threadfence();
+        atomicAdd(&hdr->heavy_done, 1u);
+      }
+      if (__syncthreads_or(bad) && t == 0) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
+    }
+  }
+
+  // ---- predictions and offsets of the rows [i0, i1)
+  if (t == 0) {
+    count_wait(&hdr->sample_done, (unsigned)G, &hdr->status);  // heavy_count is final
+    const unsigned nh = (unsigned)min((unsigned long long)flag_load(&hdr->heavy_count),
+                                      (unsigned long long)d.heavy_cap);
+    count_wait(&hdr->heavy_done, nh, &hdr->status);  // f* and z* are final
+    if (MODE == kModeReference) count_wait(&hdr->stream_done, (unsigned)G, &hdr->status);  // F
+    volatile WsHeader* vh = hdr;
+    const unsigned long long f = vh->f_acc, z = vh->z_acc;
+    ss.bc[0] = (long long)f;
+    ss.bc[1] = (long long)z;
+    ss.bc[2] = (long long)vh->s_acc;
+    ss.bc[3] = (long long)vh->F_acc;
+    ss.bc[5] = (MODE == kModePredict && f && z < f) ? (long long)pred_recip(z, f) : 0;
+  }
+  __syncthreads();
+  const unsigned long long fz = (unsigned long long)ss.bc[0], zz = (unsigned long long)ss.bc[1];
+  const unsigned long long S = (unsigned long long)ss.bc[2], F = (unsigned long long)ss.bc[3];
+  const unsigned long long R = (unsigned long long)ss.bc[5];
+  const u128 zm = (u128)zz * (u128)(unsigned long long)a.M;
+  const u128 den = (u128)F * (u128)S;
+  const double ratio_ref = (MODE == kModeReference && F > 0 && S)
+                               ? ((double)zz * (double)a.M) / ((double)F * (double)S)
+                               : 0.0;
+  bool sat = false;
+  // the prediction of one row from its FLOP: ceil(flop * z* / f*), or flop
+  // when f* = 0 (empty sample) or z* = f*
+  auto predict = [&](int v) -> int {
+    if (MODE == kModePredict) return (fz == 0 || zz >= fz) ? v : pred_fixed((uint32_t)v, zz, fz, R);
+    return S == 0 ? v : pred_reference((uint32_t)v, zm, den, ratio_ref, &sat);
+  };
+  auto flop_of = [&](int r) -> int {
+    return (flop_in_smem && r - i0 < kSFlopN) ? sflop[r - i0] : a.flop[r];
+  };
+  // pass 1: the block's total (rows in the layout of pass 2)
+  long long loc = 0;
+  for (int rb = i0; rb < i1; rb += kPredThreads * kRowsPerThread) {
+    const int r0 = rb + t * kRowsPerThread;
+    int v[kRowsPerThread];
+#pragma unroll
+    for (int u = 0; u < kRowsPerThread; ++u) v[u] = (r0 + u < i1) ? flop_of(r0 + u) : 0;
+#pragma unroll
+    for (int u = 0; u < kRowsPerThread; ++u) loc += predict(v[u]);
+  }
+  const long long blk_p = block_sum<kPredThreads>(loc, ss.red);
+  if (t == 0) {
+    slots[c].total = blk_p;
+    flag_store(&slots[c].total_flag, ep);
+  }
+  long long ppart = 0;
+  for (int q = t; q < c; q += kPredThreads) {
+    if (flag_wait(&slots[q].total_flag, ep, &hdr->status))
+      ppart += *reinterpret_cast<volatile long long*>(&slots[q].total);
+  }
+  long long run = block_sum<kPredThreads>(ppart, ss.red);
+  // pass 2: predictions and offsets.  Thread t takes the 4 rows r0 = base + 4t
+  // .. r0 + 3 of each chunk, base = i0 rounded down to a multiple of 4, so a
+  // thread whose 4 rows all belong to the block writes them with one 16-byte
+  // (pred) and two 16-byte (offsets) stores; rows outside [i0, i1) are skipped.
+  static_assert(kRowsPerThread == 4, "vector stores of 4 rows");
+  const int base0 = i0 & ~3;
+  const bool vec = ((reinterpret_cast<uintptr_t>(a.pred) | reinterpret_cast<uintptr_t>(a.offsets)) & 15) == 0;
+  for (int rb = base0; rb < i1; rb += kPredThreads * kRowsPerThread) {
+    const int r0 = rb + t * kRowsPerThread;
+    int v[kRowsPerThread];
+    long long l = 0;
+#pragma unroll
+    for (int u = 0; u < kRowsPerThread; ++u) {
+      const int r = r0 + u;
+      v[u] = (r >= i0 && r < i1) ? predict(flop_of(r)) : 0;
+      l += v[u];
+    }
+    long long tot;
+    long long ex = block_excl_scan<kPredThreads>(l, ss.red, &tot) + run;
+    if (vec && r0 >= i0 && r0 + 3 < i1) {
+      long long o[kRowsPerThread];
+#pragma unroll
+      for (int u = 0; u < kRowsPerThread; ++u) {
+        o[u] = ex;
+        ex += v[u];
+      }
+      *reinterpret_cast<int4*>(a.pred + r0) = make_int4(v[0], v[1], v[2], v[3]);
+      *reinterpret_cast<longlong2*>(a.offsets + r0) = make_longlong2(o[0], o[1]);
+      *reinterpret_cast<longlong2*>(a.offsets + r0 + 2) = make_longlong2(o[2], o[3]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < kRowsPerThread; ++u) {
+        const int r = r0 + u;
+        if (r >= i0 && r < i1) {
+          a.pred[r] = v[u];
+          a.offsets[r] = ex;
+        }
+        ex += v[u];
+      }
+    }
+    run += tot;
+  }
+  if (c == G - 1 && t == 0) {
+    a.offsets[a.M] = run;
+    a.res->pred_total = run;
+  }
+  if (__syncthreads_or(sat) && t == 0) set_status(hdr, SPGEMM_STATUS_WARN_SATURATED);
+
+  // ---- the last block to finish writes the result record and resets the header
+  if (t == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&hdr->done, 1u);
+    if (prev == (unsigned)G - 1) {
+      __threadfence();
+      volatile WsHeader* vh = hdr;
+      unsigned st = vh->status;
+      if (MODE == kModePredict ? fz == 0 : S == 0) st |= SPGEMM_STATUS_WARN_EMPTY_SAMPLE;
+      a.res->flop_total = (long long)vh->F_acc;
+      a.res->flop_s = (long long)fz;
+      a.res->nnz_s = (long long)zz;
+      a.res->n_sampled = (long long)S;
+      a.res->status = (int)st;
+      vh->f_acc = 0;
+      vh->z_acc = 0;
+      vh->s_acc = 0;
+      vh->F_acc = 0;
+      vh->heavy_count = 0;
+      vh->status = 0;
+      vh->table_done = 0;
+      vh->sample_done = 0;
+      vh->heavy_ctr = 0;
+      vh->heavy_done = 0;
+      vh->stream_done = 0;
+      vh->done = 0;
+      __threadfence();
+      vh->epoch = ep;
+    }
+  }
+}
+
+}  // namespace spg
