@@ -136,6 +136,13 @@ __device__ __forceinline__ uint64_t pred_recip(uint64_t z, uint64_t f) {
 }
 __device__ __forceinline__ int pred_fixed(uint32_t v, uint64_t z, uint64_t f, uint64_t R) {
   uint64_t q = __umul64hi((uint64_t)v, R);
+  if (f < (1ull << 32)) {  // then v * z and (q + 2) * f stay below 2^64
+    const uint64_t num = (uint64_t)v * z;
+    if (q * f >= num) return (int)q;
+    ++q;
+    if (q * f >= num) return (int)q;
+    return (int)(q + 1);
+  }
   const u128 num = (u128)v * z;
   if ((u128)q * f >= num) return (int)q;
   ++q;
@@ -278,6 +285,19 @@ __device__ __noinline__ bool flag_wait(const unsigned int* p, unsigned int want,
     if (ns < 1024) ns <<= 1;
     if (flag_load(p) == want) return true;
     if ((it & 63) == 63 && global_ns() - t0 > 1000000000ull) break;
+  }
+  atomicOr(status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);
+  return false;
+}
+
+// flag_wait for waits expected to be short: polls every 64 ns or so.
+__device__ __noinline__ bool flag_wait_short(const unsigned int* p, unsigned int want,
+                                             unsigned int* status) {
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < (1 << 26); ++it) {
+    if (flag_load(p) == want) return true;
+    __nanosleep(64);
+    if ((it & 255) == 255 && global_ns() - t0 > 1000000000ull) break;
   }
   atomicOr(status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);
   return false;

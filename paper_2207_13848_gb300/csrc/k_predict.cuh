@@ -565,18 +565,26 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
     if (MODE == kModePredict) return (fz == 0 || zz >= fz) ? v : pred_fixed((uint32_t)v, zz, fz, R);
     return S == 0 ? v : pred_reference((uint32_t)v, zm, den, ratio_ref, &sat);
   };
-  auto flop_of = [&](int r) -> int {
-    return (flop_in_smem && r - i0 < kSFlopN) ? sflop[r - i0] : a.flop[r];
-  };
-  // pass 1: the block's total (rows in the layout of pass 2)
+  // pass 1: every prediction of the block's rows, once; it replaces the FLOP
+  // in sflop (rows [i0, i0 + kSFlopN) while the FLOP is there) or goes to
+  // f.pred; and the block total.  Thread t takes rows base0 + 4t .. + 3 of each
+  // chunk (base0 = i0 rounded down to a multiple of 4), as pass 2 does.
+  static_assert(kRowsPerThread == 4, "vector stores of 4 rows");
+  const int base0 = i0 & ~3;
+  const int s_hi = flop_in_smem ? min(i1, i0 + kSFlopN) : i0;  // rows [i0, s_hi) live in sflop
   long long loc = 0;
-  for (int rb = i0; rb < i1; rb += kPredThreads * kRowsPerThread) {
+  for (int rb = base0; rb < i1; rb += kPredThreads * kRowsPerThread) {
     const int r0 = rb + t * kRowsPerThread;
-    int v[kRowsPerThread];
 #pragma unroll
-    for (int u = 0; u < kRowsPerThread; ++u) v[u] = (r0 + u < i1) ? flop_of(r0 + u) : 0;
-#pragma unroll
-    for (int u = 0; u < kRowsPerThread; ++u) loc += predict(v[u]);
+    for (int u = 0; u < kRowsPerThread; ++u) {
+      const int r = r0 + u;
+      if (r >= i0 && r < i1) {
+        const bool in_s = r < s_hi;
+        const int q = predict(in_s ? sflop[r - i0] : a.flop[r]);
+        if (in_s) sflop[r - i0] = q; else a.pred[r] = q;
+        loc += q;
+      }
+    }
   }
   const long long blk_p = block_sum<kPredThreads>(loc, ss.red);
   if (t == 0) {
@@ -585,16 +593,12 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
   }
   long long ppart = 0;
   for (int q = t; q < c; q += kPredThreads) {
-    if (flag_wait(&slots[q].total_flag, ep, &hdr->status))
+    if (flag_wait_short(&slots[q].total_flag, ep, &hdr->status))
       ppart += *reinterpret_cast<volatile long long*>(&slots[q].total);
   }
   long long run = block_sum<kPredThreads>(ppart, ss.red);
-  // pass 2: predictions and offsets.  Thread t takes the 4 rows r0 = base + 4t
-  // .. r0 + 3 of each chunk, base = i0 rounded down to a multiple of 4, so a
-  // thread whose 4 rows all belong to the block writes them with one 16-byte
-  // (pred) and two 16-byte (offsets) stores; rows outside [i0, i1) are skipped.
-  static_assert(kRowsPerThread == 4, "vector stores of 4 rows");
-  const int base0 = i0 & ~3;
+  // pass 2: offsets (and the predictions kept in sflop); a thread whose 4 rows
+  // all belong to the block writes them with 16-byte stores
   const bool vec = ((reinterpret_cast<uintptr_t>(a.pred) | reinterpret_cast<uintptr_t>(a.offsets)) & 15) == 0;
   for (int rb = base0; rb < i1; rb += kPredThreads * kRowsPerThread) {
     const int r0 = rb + t * kRowsPerThread;
@@ -603,7 +607,7 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
 #pragma unroll
     for (int u = 0; u < kRowsPerThread; ++u) {
       const int r = r0 + u;
-      v[u] = (r >= i0 && r < i1) ? predict(flop_of(r)) : 0;
+      v[u] = (r >= i0 && r < i1) ? (r < s_hi ? sflop[r - i0] : a.pred[r]) : 0;
       l += v[u];
     }
     long long tot;
