@@ -408,6 +408,119 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ other suites
+def _family_pool(sizes, variants, dev):
+    import paper_2207_13848_gb300 as sp
+    pool, names = [], []
+    for st in W.STRUCTURES:
+        for k, n in enumerate(sizes):
+            v = variants[k % len(variants)]
+            A, B, name = W.family_case(st, n, v)
+            dA = sp.DeviceCSR.from_host(A, dev)
+            dB = dA if B is A else sp.DeviceCSR.from_host(B, dev)
+            pool.append((dA, dB))
+            names.append(name)
+    return pool, names
+
+
+def run_serve(args):
+    """Serving (continuous admission into stream slots by device memory):
+    saturation throughput, then Poisson arrivals at 0.5x and 0.9x of it;
+    requests mix the five family structures at n = 2^12 .. 2^21 (log-uniform),
+    operands resident on the device, 1 % Bernoulli sample, fresh seed each."""
+    import torch
+    from paper_2207_13848_gb300 import build as spbuild
+    from paper_2207_13848_gb300 import serve
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spbuild.build()
+    sizes = [1 << e for e in range(12, 22)]
+    pool, names = _family_pool(sizes, (2, 6, 12), dev)
+    n = args.serve_requests
+    srv = serve.Server(slots=args.serve_slots, memory_budget=16 << 30, device=dev)
+    serve.run_poisson(srv, pool, rate=0, n_requests=min(n, 500), seed=99)  # warm-up (pools, caches)
+    done, _ = serve.run_poisson(srv, pool, rate=0, n_requests=n, seed=1)
+    sat = serve.latency_summary(done)
+    sat_rate = n / sat["span"]
+    levels = [{"offered": "all at once", **sat, "req_per_s": sat_rate}]
+    for f in (0.5, 0.9):
+        done, _ = serve.run_poisson(srv, pool, rate=f * sat_rate, n_requests=n, seed=int(10 * f))
+        summ = serve.latency_summary(done)
+        levels.append({"offered": f"{f} x saturation", "offered_req_per_s": f * sat_rate, **summ,
+                       "req_per_s": n / summ["span"]})
+    bad = [r for r in srv.finished if int(r.res_host[5]) & 0x300]
+    line = {"suite": "serve", "metric": "requests/s and p50/p99 latency of served predictions",
+            "n_requests": n, "slots": args.serve_slots, "pool": len(pool),
+            "pool_sizes": "n = 2^12..2^21, 5 structures", "peak_inflight": srv.stats.peak_inflight,
+            "error_results": len(bad), "levels": levels}
+    print(json.dumps(line))
+    return 0
+
+
+def run_batch(args):
+    """Batched predictor vs one spgemm_predict_structure launch per case on the
+    family (5 structures x n = 2^12..2^18 x 25 variants), same results."""
+    import torch
+    import paper_2207_13848_gb300 as sp
+    from paper_2207_13848_gb300 import build as spbuild
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spbuild.build()
+    T = threshold()
+    cases = []
+    for st in W.STRUCTURES:
+        for e in (12, 14, 16, 18):
+            for v in range(25):
+                A, B, _ = W.family_case(st, 1 << e, v)
+                dA = sp.DeviceCSR.from_host(A, dev)
+                dB = dA if B is A else sp.DeviceCSR.from_host(B, dev)
+                cases.append((dA, dB, sp.config(threshold=T, seed=v)))
+    stream = torch.cuda.current_stream()
+    # per-case launches: one workspace and output set per case, allocated up front
+    per = []
+    for dA, dB, cfg in cases:
+        ws = sp.Workspace.for_operands(dA, dB, dev)
+        pred = torch.empty(dA.rows, dtype=torch.int32, device=dev)
+        offs = torch.empty(dA.rows + 1, dtype=torch.int64, device=dev)
+        per.append((dA, dB, cfg, ws, pred, offs, sp.new_result(dev)))
+
+    def per_case():
+        for dA, dB, cfg, ws, pred, offs, res in per:
+            rc = sp.spgemm_predict_structure(dA, dB, cfg, pred, offs, None, res, ws, stream)
+            if rc != sp.OK:
+                raise RuntimeError(sp.spgemm_status_string(rc))
+
+    def timed(fn, reps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sorted(a.elapsed_time(b) for a, b in ev)
+
+    per_case()
+    t_per = timed(per_case, args.steps)
+    batch = sp.Batch(cases, device=dev)
+    best, best_ms = batch.autotune(reps=3)
+    batch.run()
+    t_batch = timed(batch.run, args.steps)
+    # same integers: every case's result record and offsets[M]
+    torch.cuda.synchronize()
+    rb = batch.results()
+    same = all(sp.read_result(per[i][6]) == rb[i] for i in range(len(cases)))
+    line = {"suite": "batch", "metric": "ms per pass over all cases: batched vs per-case launches",
+            "n_cases": len(cases), "cases": "5 structures x n=2^12..2^18 x 25 variants (2-64 nnz/row, "
+                                            "odd variants rectangular), 1% Bernoulli",
+            "per_case_ms": {"median": t_per[len(t_per) // 2], "min": t_per[0]},
+            "batch_ms": {"median": t_batch[len(t_batch) // 2], "min": t_batch[0]},
+            "speedup_median": t_per[len(t_per) // 2] / t_batch[len(t_batch) // 2],
+            "tuning": best.as_dict(), "autotune_ms": best_ms, "identical_results": same,
+            "gpu_launches_per_pass": {"per_case": len(cases), "batch": 4}}
+    print(json.dumps(line))
+    return 0 if same else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -417,11 +530,20 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--suite", choices=("predict", "serve", "batch"), default="predict",
+                    help="predict (default): the headline line; serve / batch: the serving loop "
+                         "and the batched predictor")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-slots", type=int, default=16)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite == "serve":
+        return run_serve(args)
+    if args.suite == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 
