@@ -521,6 +521,44 @@ def run_batch(args):
     return 0 if same else 1
 
 
+def run_accuracy(args):
+    """Accuracy of the proposed estimate (Z2*) against the reference design
+    (Z1*) over the synthetic family, as in Sec. VI-A: per case the exact Z from
+    the GPU symbolic phase, then mean / worst |eps1|, |eps_f|, |eps2|, the share
+    of cases where eps2 beats eps1 and corr(eps1, eps_f), for the 1 % Bernoulli
+    sample and the paper's min(0.003 M, 300) draws."""
+    import torch
+    import paper_2207_13848_gb300 as sp
+    from paper_2207_13848_gb300 import build as spbuild
+    from paper_2207_13848_gb300.report import accuracy_summary, estimates
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spbuild.build()
+    per_mode = {"bernoulli_1pct": [], "paper_draws": []}
+    for st in W.STRUCTURES:
+        for e in (12, 14, 16):
+            for v in range(25):
+                A, B, name = W.family_case(st, 1 << e, v)
+                dA = sp.DeviceCSR.from_host(A, dev)
+                dB = dA if B is A else sp.DeviceCSR.from_host(B, dev)
+                ws = sp.Workspace.for_operands(dA, dB, dev)
+                Z = sp.read_result(sp.symbolic_exact(dA, dB, ws=ws).res)["pred_total"]
+                for mode, cfg in (("bernoulli_1pct", sp.config(threshold=threshold(), seed=v)),
+                                  ("paper_draws", sp.config(mode=sp.SAMPLE_PAPER_DRAW, seed=v))):
+                    r = sp.read_result(sp.predict_structure(dA, dB, cfg, ws=ws).res)
+                    est = estimates(r["flop_total"], Z, r["flop_s"], r["nnz_s"], A.rows, r["n_sampled"])
+                    per_mode[mode].append(dict(case=name, **est))
+    line = {"suite": "accuracy", "metric": "relative error of the predicted NNZ(C), Sec. VI-A statistics",
+            "cases": "5 structures x n=2^12,2^14,2^16 x 25 variants (375), exact Z from the GPU symbolic phase",
+            "paper_context": {"mean_abs": {"eps1": 0.0812, "eps_f": 0.0859, "eps2": 0.0156},
+                              "max_abs": {"eps1": 1.58, "eps_f": 1.55, "eps2": 0.25},
+                              "eps2_better_share": 0.814, "corr_eps1_epsf": 0.9701,
+                              "note": "625 SuiteSparse cross-products on CPUs; context only"},
+            "results": {m: accuracy_summary(c) for m, c in per_mode.items()}}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -530,7 +568,7 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--suite", choices=("predict", "serve", "batch"), default="predict",
+    ap.add_argument("--suite", choices=("predict", "serve", "batch", "accuracy"), default="predict",
                     help="predict (default): the headline line; serve / batch: the serving loop "
                          "and the batched predictor")
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -544,6 +582,8 @@ def main(argv=None):
         return run_serve(args)
     if args.suite == "batch":
         return run_batch(args)
+    if args.suite == "accuracy":
+        return run_accuracy(args)
     return run_ours(args)
 
 

@@ -134,14 +134,16 @@ __device__ __forceinline__ unsigned table_load(const unsigned char* p) { return 
 // FLOP written; rows split between warps are joined here; the row split with
 // the previous range (has_prev) and the row left open at the end are reported
 // in *out (written by the group's first thread; all its threads may read it on
-// return).  ftot/ptot
-// receive this thread's share of the FLOP / prediction sums of finished rows.
+// return).  ftot/ptot receive this thread's share of the FLOP / prediction
+// sums of finished rows.  pre_wl0/pre_wl1, when not negative, are the warp's
+// row bounds for its share of [d0, d1) (found earlier by merge_path_rows2).
 template <int MODE, int NW, int WOFF = 0, int BAR = 0>
 __device__ __forceinline__ void flop_range(const FlopArgs& a, long long d0, long long d1, bool has_prev,
                                            unsigned long long fz, unsigned long long zz, double ratio,
                                            FlopSharedT<NW>& sm, RangeOut* out, long long& ftot,
                                            long long& ptot, bool& bad, int* sflop = nullptr,
-                                           int sflop_n = 0, bool flop_global = true) {
+                                           int sflop_n = 0, bool flop_global = true,
+                                           long long pre_wl0 = -1, long long pre_wl1 = -1) {
   // ---- the range is split evenly among the block's warps; each warp finds
   // both of its bounds in one pass, and the range's bounds are the first
   // warp's start and the last warp's end
@@ -151,8 +153,8 @@ __device__ __forceinline__ void flop_range(const FlopArgs& a, long long d0, long
   const int M = (int)a.M;
   const long long wd0 = d0 + (d1 - d0) * warp / NW;
   const long long wd1 = d0 + (d1 - d0) * (warp + 1) / NW;
-  long long wl0, wl1;
-  merge_path_rows2(a.a_rpt, a.M, wd0, wd1, &wl0, &wl1);
+  long long wl0 = pre_wl0, wl1 = pre_wl1;  // the warp's row bounds, when the caller found them
+  if (pre_wl0 < 0) merge_path_rows2(a.a_rpt, a.M, wd0, wd1, &wl0, &wl1);
   if (lane == 0 && warp == 0) sm.bc[0] = wl0;
   if (lane == 0 && warp == NW - 1) sm.bc[1] = wl1;
   group_sync<BAR, NW * 32>();

@@ -447,6 +447,14 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
   } else {
     // ---- streaming group: the table share, then the FLOP of the block's rows
     constexpr int L = kSampThreads;  // the group's first thread
+    const long long D = a.M + a.nnzA;
+    const long long d0 = (long long)c * D / G, d1 = (long long)(c + 1) * D / G;
+    // the warp's row bounds first: their dependent loads overlap the table
+    // share and the wait for the other blocks' shares
+    const int sw = (t >> 5) - kSampWarps;
+    long long wl0, wl1;
+    merge_path_rows2(a.a_rpt, a.M, d0 + (d1 - d0) * sw / kStreamWarps, d0 + (d1 - d0) * (sw + 1) / kStreamWarps,
+                     &wl0, &wl1);
     bool bad = false;
     degree_words(a.b_rpt, a.K, a.nnzB, a.ws.deg8, (long long)c * kStreamThreads + (t - L),
                  (long long)G * kStreamThreads, bad);
@@ -457,13 +465,11 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
       count_wait(&hdr->table_done, (unsigned)G, &hdr->status);
     }
     group_sync<kBarStream, kStreamThreads>();
-    const long long D = a.M + a.nnzA;
-    const long long d0 = (long long)c * D / G, d1 = (long long)(c + 1) * D / G;
     bad = false;
     long long ptot = 0;
     flop_range<kModeFlop, kStreamWarps, kSampWarps, kBarStream>(a, d0, d1, c > 0, 0ull, 0ull, 0.0, fs, &fs.out,
                                                                 ftot, ptot, bad, sflop, kSFlopN,
-                                                                p.flop_out != 0);
+                                                                p.flop_out != 0, wl0, wl1);
     if (group_or<kBarStream, kStreamThreads>(bad) && t == L) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
     if (t == L) {
       const long long run = fs.out.run;

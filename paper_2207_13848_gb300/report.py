@@ -37,3 +37,30 @@ def row_errors(pred, nnz):
         return {"mean": None, "max": None}
     e = np.abs(pred[m] - nnz[m]) / nnz[m]
     return {"mean": float(e.mean()), "max": float(e.max())}
+
+
+def accuracy_summary(cases):
+    """The statistics of Sec. VI-A over a list of per-case dicts with eps1,
+    eps_f, eps2 (cases where an estimate is undefined are left out of it):
+    mean and worst |eps| of each, the share of cases where |eps2| < |eps1|
+    (ties counted apart), and the correlation of eps1 and eps_f."""
+    def col(k):
+        return np.array([c[k] for c in cases if c.get(k) is not None], dtype=np.float64)
+
+    out = {"cases": len(cases)}
+    for k in ("eps1", "eps_f", "eps2"):
+        v = np.abs(col(k))
+        out[k] = {"mean_abs": float(v.mean()) if v.size else None, "max_abs": float(v.max()) if v.size else None,
+                  "n": int(v.size)}
+    both = [c for c in cases if c.get("eps1") is not None and c.get("eps2") is not None]
+    if both:
+        e1 = np.abs([c["eps1"] for c in both])
+        e2 = np.abs([c["eps2"] for c in both])
+        out["eps2_better_share"] = float(np.mean(e2 < e1))
+        out["tie_share"] = float(np.mean(e2 == e1))
+    pair = [c for c in cases if c.get("eps1") is not None and c.get("eps_f") is not None]
+    if len(pair) > 1:
+        a = np.array([c["eps1"] for c in pair])
+        b = np.array([c["eps_f"] for c in pair])
+        out["corr_eps1_epsf"] = float(np.corrcoef(a, b)[0, 1]) if a.std() > 0 and b.std() > 0 else None
+    return out
