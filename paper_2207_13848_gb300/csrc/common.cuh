@@ -50,7 +50,9 @@ struct alignas(64) Slot {
   long long carry;  // partial FLOP of the row open at the block's end
   long long total;  // sum of the block's per-row values (pred or nnz)
   long long ftot;   // sum of the block's complete-row FLOP
-  long long pad1[3];
+  unsigned long long tot_ep;  // (epoch << 32) | total, or | 0xffffffff when total
+                              // needs 32 bits or more (then read `total`)
+  long long pad1[2];
 };
 
 struct Workspace {
@@ -131,11 +133,39 @@ __device__ __forceinline__ int pred_proposed(uint32_t v, uint64_t z, uint64_t f,
 // floor(z * 2^64 / f) is prepared once (pred_recip, for 0 < z < f); then
 // q = floor(v * R / 2^64) is floor(v * z / f) or one less, and the exact ceiling
 // is q, q + 1 or q + 2, decided by two 128-bit comparisons with v * z.
-__device__ __forceinline__ uint64_t pred_recip(uint64_t z, uint64_t f) {
+__host__ __device__ __forceinline__ uint64_t pred_recip(uint64_t z, uint64_t f) {
   return (uint64_t)(((u128)z << 64) / (u128)f);
 }
-__device__ __forceinline__ int pred_fixed(uint32_t v, uint64_t z, uint64_t f, uint64_t R) {
+// pred_recip without a 128-bit division: a double estimate, then the exact
+// correction from the 128-bit remainder (the estimate is within 2^13 of R, so
+// one more double step and a final +-1 adjustment are exact).
+__host__ __device__ __forceinline__ uint64_t pred_recip_fast(uint64_t z, uint64_t f) {
+  const double ratio = (double)z / (double)f;                       // in [0, 1)
+  uint64_t R = ratio >= 1.0 ? ~0ull : (uint64_t)(ratio * 18446744073709551616.0);
+  const u128 num = (u128)z << 64;
+  // r = num - R * f, signed; |r| < 2^14 * f
+  const u128 prod = (u128)R * f;
+  if (prod <= num) {
+    const u128 r = num - prod;
+    R += (uint64_t)((double)r / (double)f);
+  } else {
+    const u128 r = prod - num;
+    R -= (uint64_t)((double)r / (double)f) + 1;
+  }
+  // final exact adjustment: R * f <= num < (R + 1) * f
+#pragma unroll 1
+  for (int it = 0; it < 4 && (u128)R * f > num; ++it) --R;
+#pragma unroll 1
+  for (int it = 0; it < 4 && (u128)(R + 1) * f <= num; ++it) ++R;
+  return R;
+}
+
+__host__ __device__ __forceinline__ int pred_fixed(uint32_t v, uint64_t z, uint64_t f, uint64_t R) {
+#ifdef __CUDA_ARCH__
   uint64_t q = __umul64hi((uint64_t)v, R);
+#else
+  uint64_t q = (uint64_t)(((u128)v * R) >> 64);
+#endif
   if (f < (1ull << 32)) {  // then v * z and (q + 2) * f stay below 2^64
     const uint64_t num = (uint64_t)v * z;
     if (q * f >= num) return (int)q;
@@ -267,6 +297,14 @@ __device__ __forceinline__ unsigned int flag_load(const unsigned int* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void word_store(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long word_load(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -301,6 +339,36 @@ __device__ __noinline__ bool flag_wait_short(const unsigned int* p, unsigned int
   }
   atomicOr(status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);
   return false;
+}
+
+// count_wait for waits expected to be short: polls every 64 ns or so.
+__device__ __noinline__ bool count_wait_short(const unsigned int* p, unsigned int want,
+                                              unsigned int* status) {
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < (1 << 26); ++it) {
+    if (flag_load(p) >= want) return true;
+    __nanosleep(64);
+    if ((it & 255) == 255 && global_ns() - t0 > 1000000000ull) break;
+  }
+  atomicOr(status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);
+  return false;
+}
+
+// The block total published in slot->tot_ep for epoch ep (one load in the
+// common case); polls every 64 ns or so and gives up like flag_wait.
+__device__ __noinline__ long long slot_total(const Slot* slot, unsigned ep, unsigned int* status) {
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < (1 << 26); ++it) {
+    const unsigned long long w = word_load(&slot->tot_ep);
+    if ((unsigned)(w >> 32) == ep) {
+      const unsigned lo = (unsigned)w;
+      return lo != 0xffffffffu ? (long long)lo : *reinterpret_cast<const volatile long long*>(&slot->total);
+    }
+    __nanosleep(64);
+    if ((it & 255) == 255 && global_ns() - t0 > 1000000000ull) break;
+  }
+  atomicOr(status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);
+  return 0;
 }
 
 // Waits until *p >= want (a counter that only grows within a launch); gives up

@@ -384,6 +384,12 @@ __device__ void sample_per_warp(const DedupArgs& d, int* tables, int* list, long
 // sampling group has finished).  Waits for an entry whose writer has not
 // stored it yet.
 __device__ int claim_heavy_row(WsHeader* hdr, int* heavy, unsigned long long cap, unsigned G) {
+  // nothing to take once every sampling group is done and every queued entry
+  // has been claimed (one round trip instead of a claim and its checks)
+  if (flag_load(&hdr->sample_done) >= G) {
+    volatile WsHeader* vh = hdr;
+    if ((unsigned long long)vh->heavy_ctr >= min((unsigned long long)vh->heavy_count, cap)) return 0;
+  }
   const unsigned h = atomicAdd(&hdr->heavy_ctr, 1u);
   const uint64_t t0 = global_ns();
   unsigned ns = 32;
@@ -449,21 +455,20 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
     constexpr int L = kSampThreads;  // the group's first thread
     const long long D = a.M + a.nnzA;
     const long long d0 = (long long)c * D / G, d1 = (long long)(c + 1) * D / G;
-    // the warp's row bounds first: their dependent loads overlap the table
-    // share and the wait for the other blocks' shares
-    const int sw = (t >> 5) - kSampWarps;
-    long long wl0, wl1;
-    merge_path_rows2(a.a_rpt, a.M, d0 + (d1 - d0) * sw / kStreamWarps, d0 + (d1 - d0) * (sw + 1) / kStreamWarps,
-                     &wl0, &wl1);
     bool bad = false;
     degree_words(a.b_rpt, a.K, a.nnzB, a.ws.deg8, (long long)c * kStreamThreads + (t - L),
                  (long long)G * kStreamThreads, bad);
     if (group_or<kBarStream, kStreamThreads>(bad) && t == L) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
-    if (t == L) {
+    if (t == L) {  // this block's share of the table is written
       __threadfence();
       atomicAdd(&hdr->table_done, 1u);
-      count_wait(&hdr->table_done, (unsigned)G, &hdr->status);
     }
+    // the warp's row bounds while the other blocks finish their shares
+    const int sw = (t >> 5) - kSampWarps;
+    long long wl0, wl1;
+    merge_path_rows2(a.a_rpt, a.M, d0 + (d1 - d0) * sw / kStreamWarps, d0 + (d1 - d0) * (sw + 1) / kStreamWarps,
+                     &wl0, &wl1);
+    if (t == L) count_wait_short(&hdr->table_done, (unsigned)G, &hdr->status);
     group_sync<kBarStream, kStreamThreads>();
     bad = false;
     long long ptot = 0;
@@ -542,18 +547,18 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
 
   // ---- predictions and offsets of the rows [i0, i1)
   if (t == 0) {
-    count_wait(&hdr->sample_done, (unsigned)G, &hdr->status);  // heavy_count is final
+    count_wait_short(&hdr->sample_done, (unsigned)G, &hdr->status);  // heavy_count is final
     const unsigned nh = (unsigned)min((unsigned long long)flag_load(&hdr->heavy_count),
                                       (unsigned long long)d.heavy_cap);
-    count_wait(&hdr->heavy_done, nh, &hdr->status);  // f* and z* are final
-    if (MODE == kModeReference) count_wait(&hdr->stream_done, (unsigned)G, &hdr->status);  // F
+    count_wait_short(&hdr->heavy_done, nh, &hdr->status);  // f* and z* are final
+    if (MODE == kModeReference) count_wait_short(&hdr->stream_done, (unsigned)G, &hdr->status);  // F
     volatile WsHeader* vh = hdr;
     const unsigned long long f = vh->f_acc, z = vh->z_acc;
     ss.bc[0] = (long long)f;
     ss.bc[1] = (long long)z;
     ss.bc[2] = (long long)vh->s_acc;
     ss.bc[3] = (long long)vh->F_acc;
-    ss.bc[5] = (MODE == kModePredict && f && z < f) ? (long long)pred_recip(z, f) : 0;
+    ss.bc[5] = (MODE == kModePredict && f && z < f) ? (long long)pred_recip_fast(z, f) : 0;
   }
   __syncthreads();
   const unsigned long long fz = (unsigned long long)ss.bc[0], zz = (unsigned long long)ss.bc[1];
@@ -593,15 +598,14 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
     }
   }
   const long long blk_p = block_sum<kPredThreads>(loc, ss.red);
-  if (t == 0) {
+  if (t == 0) {  // the total with its epoch in one word (and in full when it needs 32 bits or more)
     slots[c].total = blk_p;
-    flag_store(&slots[c].total_flag, ep);
+    const unsigned lo = blk_p < 0xffffffffll ? (unsigned)blk_p : 0xffffffffu;
+    if (lo == 0xffffffffu) __threadfence();
+    word_store(&slots[c].tot_ep, ((unsigned long long)ep << 32) | lo);
   }
   long long ppart = 0;
-  for (int q = t; q < c; q += kPredThreads) {
-    if (flag_wait_short(&slots[q].total_flag, ep, &hdr->status))
-      ppart += *reinterpret_cast<volatile long long*>(&slots[q].total);
-  }
+  for (int q = t; q < c; q += kPredThreads) ppart += slot_total(&slots[q], ep, &hdr->status);
   long long run = block_sum<kPredThreads>(ppart, ss.red);
   // pass 2: offsets (and the predictions kept in sflop); a thread whose 4 rows
   // all belong to the block writes them with 16-byte stores
