@@ -180,6 +180,35 @@ __host__ __device__ __forceinline__ int pred_fixed(uint32_t v, uint64_t z, uint6
   return (int)(q + 1);
 }
 
+// ceil(v * z / f) for f < 2^32 (and z < f), with R32 = floor(z * 2^32 / f):
+// v * R32 / 2^32 <= v * z / f < v * R32 / 2^32 + v / 2^32, and v < 2^32, so
+// q = floor(v * R32 / 2^32) is floor(v * z / f) or one less; the remainder
+// v * z - q * f (64-bit products of 32-bit operands, in [0, 2f)) settles it.
+__host__ __device__ __forceinline__ uint32_t pred_recip32(uint32_t z, uint32_t f) {
+  return (uint32_t)(((uint64_t)z << 32) / f);
+}
+__host__ __device__ __forceinline__ int pred_ceil32(uint32_t v, uint32_t z, uint32_t f, uint32_t R32) {
+#ifdef __CUDA_ARCH__
+  uint32_t q = __umulhi(v, R32);
+#else
+  uint32_t q = (uint32_t)(((uint64_t)v * R32) >> 32);
+#endif
+  uint64_t r = (uint64_t)v * z - (uint64_t)q * f;
+  if (r >= f) {
+    ++q;
+    r -= f;
+  }
+  return (int)(q + (r != 0));
+}
+// The reciprocal that pred_fast takes (z < f): 32-bit when f < 2^32, else 64.64.
+__host__ __device__ __forceinline__ uint64_t pred_recip_any(uint64_t z, uint64_t f) {
+  return f < (1ull << 32) ? pred_recip32((uint32_t)z, (uint32_t)f) : pred_recip_fast(z, f);
+}
+// ceil(v * z / f) for z < f, with R = pred_recip_any(z, f).
+__host__ __device__ __forceinline__ int pred_fast(uint32_t v, uint64_t z, uint64_t f, uint64_t R) {
+  return f < (1ull << 32) ? pred_ceil32(v, (uint32_t)z, (uint32_t)f, (uint32_t)R) : pred_fixed(v, z, f, R);
+}
+
 // ceil(v * zm / den) for the reference design: zm = z * M (< 2^94),
 // den = F * |S| (< 2^94).  Saturates at 2^31 - 1 and reports it via *sat.
 __device__ __forceinline__ int pred_reference(uint32_t v, u128 zm, u128 den, double ratio,
@@ -394,28 +423,62 @@ __device__ __forceinline__ void set_status(WsHeader* h, unsigned bits) { atomicO
 // in the FLOP pass (fewer L2 sectors and more L1 reuse); kDegEscape means
 // "read B.rpt".  Offsets out of range give 0 and set *bad.  Thread `first` of
 // `nthreads` writes the 4-row words first, first + nthreads, ...
+// The table word of rows [k0, k0 + 4) from v[u] = B.rpt[k0 + u] (u <= 4, entries past K unused).
+__device__ __forceinline__ unsigned degree_word(const int* v, long long k0, long long K, long long nnzB,
+                                                bool& bad) {
+  unsigned word = 0;
+  long long prev = v[0];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (k0 + u < K) {
+      const long long next = v[u + 1];
+      long long d = next - prev;
+      if (d < 0 || prev < 0 || next > nnzB) {
+        bad = true;
+        d = 0;
+      }
+      word |= (unsigned)(d < kDegEscape ? d : kDegEscape) << (8 * u);
+      prev = next;
+    }
+  }
+  return word;
+}
+
 __device__ __forceinline__ void degree_words(const int* b_rpt, long long K, long long nnzB,
                                              unsigned char* deg8, long long first, long long nthreads,
                                              bool& bad) {
   for (long long k0 = first * 4; k0 < K; k0 += nthreads * 4) {
-    unsigned word = 0;
-    long long prev = __ldg(b_rpt + k0);
+    int v[5];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (k0 + u < K) {
-        const long long next = __ldg(b_rpt + k0 + u + 1);
-        long long d = next - prev;
-        if (d < 0 || prev < 0 || next > nnzB) {
-          bad = true;
-          d = 0;
-        }
-        word |= (unsigned)(d < kDegEscape ? d : kDegEscape) << (8 * u);
-        prev = next;
-      }
-    }
-    *reinterpret_cast<unsigned*>(deg8 + k0) = word;
+    for (int u = 0; u < 5; ++u) v[u] = k0 + u <= K ? __ldg(b_rpt + k0 + u) : 0;
+    *reinterpret_cast<unsigned*>(deg8 + k0) = degree_word(v, k0, K, nnzB, bad);
   }
 }
+
+// degree_words with the loads of the thread's first NB words issued at once:
+// load() reads their B.rpt entries, store() writes those words and then the
+// thread's remaining ones.
+template <int NB>
+struct DegreeBatch {
+  int v[NB][5];
+  __device__ __forceinline__ void load(const int* b_rpt, long long K, long long first, long long nthreads) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const long long k0 = (first + b * nthreads) * 4;
+#pragma unroll
+      for (int u = 0; u < 5; ++u) v[b][u] = k0 + u <= K ? __ldg(b_rpt + k0 + u) : 0;
+    }
+  }
+  __device__ __forceinline__ void store(const int* b_rpt, long long K, long long nnzB, unsigned char* deg8,
+                                        long long first, long long nthreads, bool& bad) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const long long k0 = (first + b * nthreads) * 4;
+      if (k0 < K) *reinterpret_cast<unsigned*>(deg8 + k0) = degree_word(v[b], k0, K, nnzB, bad);
+    }
+    degree_words(b_rpt, K, nnzB, deg8, first + NB * nthreads, nthreads, bad);
+  }
+};
 
 __global__ void k_degree_table(const int* b_rpt, long long K, long long nnzB, unsigned char* deg8,
                                WsHeader* hdr) {

@@ -160,11 +160,14 @@ __device__ __forceinline__ void flop_range(const FlopArgs& a, long long d0, long
   group_sync<BAR, NW * 32>();
   const long long bi0 = sm.bc[0], bi1 = sm.bc[1];
   const int i0 = (int)bi0, i1 = (int)bi1;
-  // FLOP mode: the block's row r goes to sflop[r - i0] when it fits there, and
-  // to a.flop[r] when flop_global or when it does not fit
+  // FLOP mode: the block's row r goes to sflop[r - (i0 & ~3)] when it fits
+  // there (so that groups of 4 rows starting at a multiple of 4 are 16-byte
+  // aligned in shared memory), and to a.flop[r] when flop_global or when it
+  // does not fit
   auto store_flop = [&](int r, int v) {
-    const bool in_s = sflop != nullptr && (unsigned)(r - i0) < (unsigned)sflop_n;
-    if (in_s) sflop[r - i0] = v;
+    const int o = r - (i0 & ~3);
+    const bool in_s = sflop != nullptr && (unsigned)o < (unsigned)sflop_n;
+    if (in_s) sflop[o] = v;
     if (flop_global || !in_s) a.flop[r] = v;
   };
   const int j0 = (int)min(max(d0 - bi0, 0ll), (long long)a.nnzA);

@@ -29,6 +29,8 @@
 // is held to 128 KB so that the FLOP pass keeps a large L1.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "k_dedup.cuh"
 #include "k_flop.cuh"
@@ -50,6 +52,8 @@ constexpr int kStreamWarps = kPredWarps - kSampWarps;
 constexpr int kStreamThreads = kStreamWarps * 32;
 constexpr int kBarSamp = 1;    // hardware barrier of the sampling group
 constexpr int kBarStream = 2;  // hardware barrier of the streaming group
+constexpr int kDegBatch = 3;    // table words per streaming thread loaded at once (2^20 rows: 2.7 each)
+constexpr int kScanChunks = 2;  // blocks of at most this many 4096-row chunks scan before the cross-block wait
 
 // ---- sampling group: batch limits ------------------------------------------------
 constexpr int kSRows = kSampThreads;            // sampled rows per row round (one per thread)
@@ -111,6 +115,9 @@ struct PredStatic {
   long long red[kPredWarps + 1];     // whole-block scans
   long long red_s[kSampWarps + 1];   // sampling-group scans
   long long bc[8];
+  unsigned long long pre[4];         // f*, z*, |S| and the ratio's reciprocal, read early
+  int pre_ready;                     // 1: pre[] is final and no sampled row is heavy
+  int stream_fin;                    // the streaming group has finished its FLOP pass
   int s_enc;
   int list[kListCapW];
   HeavySmem heavy;
@@ -429,6 +436,11 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
   int* sflop = reinterpret_cast<int*>(pdyn + kOffSflop);
   FlopSharedT<kStreamWarps>& fs = *reinterpret_cast<FlopSharedT<kStreamWarps>*>(pdyn + kOffFlopSm);
   long long ftot = 0;  // streaming threads: FLOP of the finished rows they wrote
+  if (t == 0) {
+    ss.pre_ready = 0;
+    ss.stream_fin = 0;
+  }
+  __syncthreads();
 
   if (t < kSampThreads) {
     // ---- sampling group: this block's slice of the sample candidates
@@ -449,6 +461,30 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
       if (s) atomicAdd(&hdr->s_acc, (unsigned long long)s);
       __threadfence();
       atomicAdd(&hdr->sample_done, 1u);
+      // f*, z* and |S| are final once every block's sampling group is done;
+      // when no sampled row was queued as heavy, read them now, while the
+      // streaming group is still busy, so that the prediction can start as
+      // soon as the FLOP pass ends.  Stops polling when the streaming group
+      // finishes first (the prediction phase then waits as usual).
+      const uint64_t t0 = global_ns();
+      for (unsigned ns = 64;;) {
+        if (flag_load(&hdr->sample_done) >= (unsigned)G) {
+          volatile WsHeader* vh = hdr;
+          if (vh->heavy_count == 0) {
+            const unsigned long long fv = vh->f_acc, zv = vh->z_acc;
+            ss.pre[0] = fv;
+            ss.pre[1] = zv;
+            ss.pre[2] = vh->s_acc;
+            ss.pre[3] = (MODE == kModePredict && fv && zv < fv) ? pred_recip_any(zv, fv) : 0;
+            ss.pre_ready = 1;
+          }
+          break;
+        }
+        if (*reinterpret_cast<volatile int*>(&ss.stream_fin)) break;
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+        if (global_ns() - t0 > 1000000000ull) break;  // the prediction phase's waits report it
+      }
     }
   } else {
     // ---- streaming group: the table share, then the FLOP of the block's rows
@@ -456,8 +492,12 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
     const long long D = a.M + a.nnzA;
     const long long d0 = (long long)c * D / G, d1 = (long long)(c + 1) * D / G;
     bool bad = false;
-    degree_words(a.b_rpt, a.K, a.nnzB, a.ws.deg8, (long long)c * kStreamThreads + (t - L),
-                 (long long)G * kStreamThreads, bad);
+    // the block's share of the B row-length table (all of a thread's loads
+    // in flight at once)
+    const long long tfirst = (long long)c * kStreamThreads + (t - L), tstride = (long long)G * kStreamThreads;
+    DegreeBatch<kDegBatch> deg;
+    deg.load(a.b_rpt, a.K, tfirst, tstride);
+    deg.store(a.b_rpt, a.K, a.nnzB, a.ws.deg8, tfirst, tstride, bad);
     if (group_or<kBarStream, kStreamThreads>(bad) && t == L) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
     if (t == L) {  // this block's share of the table is written
       __threadfence();
@@ -483,7 +523,7 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
       // the FLOP of a row that spans blocks (waits only on block c - 1)
       if (fs.out.dep) {
         long long cin = 0;
-        if (flag_wait(&slots[c - 1].carry_flag, ep, &hdr->status)) cin = slots[c - 1].carry;
+        if (flag_wait_short(&slots[c - 1].carry_flag, ep, &hdr->status)) cin = slots[c - 1].carry;
         slots[c].carry = cin + run;
         flag_store(&slots[c].carry_flag, ep);
       } else {
@@ -491,9 +531,9 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
         flag_store(&slots[c].carry_flag, ep);
         if (fs.out.head_pending) {
           long long cin = 0;
-          if (flag_wait(&slots[c - 1].carry_flag, ep, &hdr->status)) cin = slots[c - 1].carry;
+          if (flag_wait_short(&slots[c - 1].carry_flag, ep, &hdr->status)) cin = slots[c - 1].carry;
           const long long v = cin + fs.out.head_known;
-          sflop[0] = (int)v;
+          sflop[i0 & 3] = (int)v;  // row i0 (sflop starts at row i0 & ~3)
           if (p.flop_out) a.flop[i0] = (int)v;
           extra_f += v;
         }
@@ -501,6 +541,7 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
       ss.bc[4] = extra_f;
       ss.bc[6] = i0;
       ss.bc[7] = i1;
+      *reinterpret_cast<volatile int*>(&ss.stream_fin) = 1;
     }
   }
   __syncthreads();
@@ -511,23 +552,27 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
     const long long blk_f = block_sum<kPredThreads>(ftot, ss.red) + ss.bc[4];
     if (t == 0) {
       atomicAdd(&hdr->F_acc, (unsigned long long)blk_f);
-      __threadfence();
-      atomicAdd(&hdr->stream_done, 1u);
+      if (MODE == kModeReference) {  // F is needed before any prediction
+        __threadfence();
+        atomicAdd(&hdr->stream_done, 1u);
+      }
     }
   }
+  // no sampled row is heavy anywhere, and f*, z*, |S| are already known
+  const bool pre = ss.pre_ready == 1;
 
   // ---- heavy sampled rows, one at a time, by the whole block
-  bool flop_in_smem = true;  // the FLOP of rows [i0, i0 + kSFlopN) is in sflop
+  bool flop_in_smem = true;  // the FLOP of rows [i0, (i0 & ~3) + kSFlopN) is in sflop
   {
     unsigned* tab = reinterpret_cast<unsigned*>(pdyn);
-    for (;;) {
+    while (!pre) {
       if (t == 0) ss.s_enc = claim_heavy_row(hdr, d.heavy, (unsigned long long)d.heavy_cap, (unsigned)G);
       __syncthreads();
       const int enc = ss.s_enc;
       if (enc == 0) break;
       if (flop_in_smem) {  // the table below overwrites sflop: move it to f.flop first
         if (!p.flop_out)
-          for (int r = i0 + t; r < min(i1, i0 + kSFlopN); r += kPredThreads) a.flop[r] = sflop[r - i0];
+          for (int r = i0 + t; r < min(i1, (i0 & ~3) + kSFlopN); r += kPredThreads) a.flop[r] = sflop[r - (i0 & ~3)];
         flop_in_smem = false;
         __syncthreads();
       }
@@ -547,18 +592,28 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
 
   // ---- predictions and offsets of the rows [i0, i1)
   if (t == 0) {
-    count_wait_short(&hdr->sample_done, (unsigned)G, &hdr->status);  // heavy_count is final
-    const unsigned nh = (unsigned)min((unsigned long long)flag_load(&hdr->heavy_count),
-                                      (unsigned long long)d.heavy_cap);
-    count_wait_short(&hdr->heavy_done, nh, &hdr->status);  // f* and z* are final
-    if (MODE == kModeReference) count_wait_short(&hdr->stream_done, (unsigned)G, &hdr->status);  // F
-    volatile WsHeader* vh = hdr;
-    const unsigned long long f = vh->f_acc, z = vh->z_acc;
-    ss.bc[0] = (long long)f;
-    ss.bc[1] = (long long)z;
-    ss.bc[2] = (long long)vh->s_acc;
-    ss.bc[3] = (long long)vh->F_acc;
-    ss.bc[5] = (MODE == kModePredict && f && z < f) ? (long long)pred_recip_fast(z, f) : 0;
+    if (pre) {
+      ss.bc[0] = (long long)ss.pre[0];
+      ss.bc[1] = (long long)ss.pre[1];
+      ss.bc[2] = (long long)ss.pre[2];
+      ss.bc[5] = (long long)ss.pre[3];
+    } else {
+      count_wait_short(&hdr->sample_done, (unsigned)G, &hdr->status);  // heavy_count is final
+      const unsigned nh = (unsigned)min((unsigned long long)flag_load(&hdr->heavy_count),
+                                        (unsigned long long)d.heavy_cap);
+      count_wait_short(&hdr->heavy_done, nh, &hdr->status);  // f* and z* are final
+      volatile WsHeader* vh = hdr;
+      const unsigned long long f = vh->f_acc, z = vh->z_acc;
+      ss.bc[0] = (long long)f;
+      ss.bc[1] = (long long)z;
+      ss.bc[2] = (long long)vh->s_acc;
+      ss.bc[5] = (MODE == kModePredict && f && z < f) ? (long long)pred_recip_any(z, f) : 0;
+    }
+    ss.bc[3] = 0;
+    if (MODE == kModeReference) {  // F
+      count_wait_short(&hdr->stream_done, (unsigned)G, &hdr->status);
+      ss.bc[3] = (long long)*reinterpret_cast<volatile unsigned long long*>(&hdr->F_acc);
+    }
   }
   __syncthreads();
   const unsigned long long fz = (unsigned long long)ss.bc[0], zz = (unsigned long long)ss.bc[1];
@@ -571,31 +626,76 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
                                : 0.0;
   bool sat = false;
   // the prediction of one row from its FLOP: ceil(flop * z* / f*), or flop
-  // when f* = 0 (empty sample) or z* = f*
-  auto predict = [&](int v) -> int {
-    if (MODE == kModePredict) return (fz == 0 || zz >= fz) ? v : pred_fixed((uint32_t)v, zz, fz, R);
+  // when f* = 0 (empty sample) or z* = f*; F32 (f* < 2^32) picks the 32-bit
+  // exact ceiling, with R the matching reciprocal (pred_recip_any)
+  auto predict = [&](int v, auto f32) -> int {
+    if (MODE == kModePredict) {
+      if (fz == 0 || zz >= fz) return v;
+      if constexpr (decltype(f32)::value) {
+        return pred_ceil32((uint32_t)v, (uint32_t)zz, (uint32_t)fz, (uint32_t)R);
+      } else {
+        return pred_fixed((uint32_t)v, zz, fz, R);
+      }
+    }
     return S == 0 ? v : pred_reference((uint32_t)v, zm, den, ratio_ref, &sat);
   };
+  const bool f32 = fz < (1ull << 32);
   // pass 1: every prediction of the block's rows, once; it replaces the FLOP
-  // in sflop (rows [i0, i0 + kSFlopN) while the FLOP is there) or goes to
-  // f.pred; and the block total.  Thread t takes rows base0 + 4t .. + 3 of each
-  // chunk (base0 = i0 rounded down to a multiple of 4), as pass 2 does.
+  // in sflop (row r at sflop[r - base0] while the FLOP is there) or goes to
+  // f.pred.  Thread t takes rows base0 + 4t .. + 3 of each chunk of
+  // kPredThreads * 4 rows (base0 = i0 rounded down to a multiple of 4), as
+  // pass 2 does.  The block total is published as soon as it is known; a
+  // block of at most kScanChunks chunks then scans them while the blocks
+  // before it publish theirs, keeping each thread's exclusive prefixes in
+  // registers, so that only the stores remain after the wait.
   static_assert(kRowsPerThread == 4, "vector stores of 4 rows");
+  constexpr int kChunkRows = kPredThreads * kRowsPerThread;
   const int base0 = i0 & ~3;
-  const int s_hi = flop_in_smem ? min(i1, i0 + kSFlopN) : i0;  // rows [i0, s_hi) live in sflop
-  long long loc = 0;
-  for (int rb = base0; rb < i1; rb += kPredThreads * kRowsPerThread) {
-    const int r0 = rb + t * kRowsPerThread;
+  const int s_hi = flop_in_smem ? min(i1, base0 + kSFlopN) : i0;  // rows [i0, s_hi) live in sflop
+  const int nchunks = i1 > base0 ? (i1 - base0 + kChunkRows - 1) / kChunkRows : 0;
+  const bool early = nchunks <= kScanChunks;
+  auto pred_rows_t = [&](int r0, auto f32t) -> long long {  // predictions of rows r0 .. r0 + 3 in place; their sum
+    long long l = 0;
+    if (r0 >= i0 && r0 + 3 < s_hi) {  // all four in sflop: one 16-byte load and store
+      int4* p4 = reinterpret_cast<int4*>(sflop + (r0 - base0));
+      int4 x = *p4;
+      x.x = predict(x.x, f32t);
+      x.y = predict(x.y, f32t);
+      x.z = predict(x.z, f32t);
+      x.w = predict(x.w, f32t);
+      *p4 = x;
+      return (long long)x.x + x.y + x.z + x.w;
+    }
 #pragma unroll
     for (int u = 0; u < kRowsPerThread; ++u) {
       const int r = r0 + u;
       if (r >= i0 && r < i1) {
         const bool in_s = r < s_hi;
-        const int q = predict(in_s ? sflop[r - i0] : a.flop[r]);
-        if (in_s) sflop[r - i0] = q; else a.pred[r] = q;
-        loc += q;
+        const int q = predict(in_s ? sflop[r - base0] : a.flop[r], f32t);
+        if (in_s) sflop[r - base0] = q; else a.pred[r] = q;
+        l += q;
       }
     }
+    return l;
+  };
+  long long lsum[kScanChunks];  // early: the thread's sum over its rows of each chunk
+  long long loc = 0;
+  // the whole pass for one arithmetic path (f32 is the same for every row)
+  auto pass1 = [&](auto f32t) {
+    if (early) {
+#pragma unroll
+      for (int ch = 0; ch < kScanChunks; ++ch) {
+        lsum[ch] = ch < nchunks ? pred_rows_t(base0 + ch * kChunkRows + t * kRowsPerThread, f32t) : 0;
+        loc += lsum[ch];
+      }
+    } else {
+      for (int rb = base0; rb < i1; rb += kChunkRows) loc += pred_rows_t(rb + t * kRowsPerThread, f32t);
+    }
+  };
+  if (f32) {
+    pass1(std::true_type{});
+  } else {
+    pass1(std::false_type{});
   }
   const long long blk_p = block_sum<kPredThreads>(loc, ss.red);
   if (t == 0) {  // the total with its epoch in one word (and in full when it needs 32 bits or more)
@@ -604,50 +704,108 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
     if (lo == 0xffffffffu) __threadfence();
     word_store(&slots[c].tot_ep, ((unsigned long long)ep << 32) | lo);
   }
-  long long ppart = 0;
-  for (int q = t; q < c; q += kPredThreads) ppart += slot_total(&slots[q], ep, &hdr->status);
-  long long run = block_sum<kPredThreads>(ppart, ss.red);
-  // pass 2: offsets (and the predictions kept in sflop); a thread whose 4 rows
-  // all belong to the block writes them with 16-byte stores
-  const bool vec = ((reinterpret_cast<uintptr_t>(a.pred) | reinterpret_cast<uintptr_t>(a.offsets)) & 15) == 0;
-  for (int rb = base0; rb < i1; rb += kPredThreads * kRowsPerThread) {
-    const int r0 = rb + t * kRowsPerThread;
-    int v[kRowsPerThread];
+  long long ex_c[kScanChunks];  // early: exclusive prefix, within the block, of the thread's rows per chunk
+  if (early) {
+    long long run_b = 0;
+#pragma unroll
+    for (int ch = 0; ch < kScanChunks; ++ch) {
+      ex_c[ch] = 0;
+      if (ch < nchunks) {  // the same for the whole block
+        long long tot;
+        ex_c[ch] = block_excl_scan<kPredThreads>(lsum[ch], ss.red, &tot) + run_b;
+        run_b += tot;
+      }
+    }
+  }
+  // the predictions of rows r0 .. r0 + 3 (from sflop or f.pred), 0 outside the block
+  auto load_rows = [&](int r0, int* v) {
+    if (r0 >= i0 && r0 + 3 < s_hi) {
+      const int4 x = *reinterpret_cast<const int4*>(sflop + (r0 - base0));
+      v[0] = x.x;
+      v[1] = x.y;
+      v[2] = x.z;
+      v[3] = x.w;
+      return (long long)x.x + x.y + x.z + x.w;
+    }
     long long l = 0;
 #pragma unroll
     for (int u = 0; u < kRowsPerThread; ++u) {
       const int r = r0 + u;
-      v[u] = (r >= i0 && r < i1) ? (r < s_hi ? sflop[r - i0] : a.pred[r]) : 0;
+      v[u] = (r >= i0 && r < i1) ? (r < s_hi ? sflop[r - base0] : a.pred[r]) : 0;
       l += v[u];
     }
-    long long tot;
-    long long ex = block_excl_scan<kPredThreads>(l, ss.red, &tot) + run;
+    return l;
+  };
+  // their stores: predictions, and offsets from ex (16-byte stores when all
+  // four rows belong to the block)
+  const bool vec = ((reinterpret_cast<uintptr_t>(a.pred) | reinterpret_cast<uintptr_t>(a.offsets)) & 15) == 0;
+  auto store_pred = [&](int r0, const int* v) {
     if (vec && r0 >= i0 && r0 + 3 < i1) {
-      long long o[kRowsPerThread];
-#pragma unroll
-      for (int u = 0; u < kRowsPerThread; ++u) {
-        o[u] = ex;
-        ex += v[u];
-      }
       *reinterpret_cast<int4*>(a.pred + r0) = make_int4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < kRowsPerThread; ++u)
+        if (r0 + u >= i0 && r0 + u < i1) a.pred[r0 + u] = v[u];
+    }
+  };
+  auto store_offsets = [&](int r0, const int* v, long long ex) {
+    long long o[kRowsPerThread];
+#pragma unroll
+    for (int u = 0; u < kRowsPerThread; ++u) {
+      o[u] = ex;
+      ex += v[u];
+    }
+    if (vec && r0 >= i0 && r0 + 3 < i1) {
       *reinterpret_cast<longlong2*>(a.offsets + r0) = make_longlong2(o[0], o[1]);
       *reinterpret_cast<longlong2*>(a.offsets + r0 + 2) = make_longlong2(o[2], o[3]);
     } else {
 #pragma unroll
-      for (int u = 0; u < kRowsPerThread; ++u) {
-        const int r = r0 + u;
-        if (r >= i0 && r < i1) {
-          a.pred[r] = v[u];
-          a.offsets[r] = ex;
-        }
-        ex += v[u];
+      for (int u = 0; u < kRowsPerThread; ++u)
+        if (r0 + u >= i0 && r0 + u < i1) a.offsets[r0 + u] = o[u];
+    }
+  };
+  // early: the predictions do not depend on the other blocks, so they are
+  // stored while the blocks before this one publish their totals
+  if (early) {
+#pragma unroll
+    for (int ch = 0; ch < kScanChunks; ++ch) {
+      if (ch < nchunks) {
+        const int r0 = base0 + ch * kChunkRows + t * kRowsPerThread;
+        int v[kRowsPerThread];
+        load_rows(r0, v);
+        store_pred(r0, v);
       }
     }
-    run += tot;
+  }
+  long long ppart = 0;
+  for (int q = t; q < c; q += kPredThreads) ppart += slot_total(&slots[q], ep, &hdr->status);
+  const long long before = block_sum<kPredThreads>(ppart, ss.red);  // predicted nnz of blocks 0 .. c-1
+  // pass 2: the offsets (with the predictions, for a block of more chunks)
+  if (early) {
+#pragma unroll
+    for (int ch = 0; ch < kScanChunks; ++ch) {
+      if (ch < nchunks) {
+        const int r0 = base0 + ch * kChunkRows + t * kRowsPerThread;
+        int v[kRowsPerThread];
+        load_rows(r0, v);
+        store_offsets(r0, v, before + ex_c[ch]);
+      }
+    }
+  } else {
+    long long run = before;
+    for (int rb = base0; rb < i1; rb += kChunkRows) {
+      const int r0 = rb + t * kRowsPerThread;
+      int v[kRowsPerThread];
+      long long tot;
+      const long long ex = block_excl_scan<kPredThreads>(load_rows(r0, v), ss.red, &tot) + run;
+      store_pred(r0, v);
+      store_offsets(r0, v, ex);
+      run += tot;
+    }
   }
   if (c == G - 1 && t == 0) {
-    a.offsets[a.M] = run;
-    a.res->pred_total = run;
+    a.offsets[a.M] = before + blk_p;
+    a.res->pred_total = before + blk_p;
   }
   if (__syncthreads_or(sat) && t == 0) set_status(hdr, SPGEMM_STATUS_WARN_SATURATED);
 

@@ -1,7 +1,8 @@
 // Host-side check of the exact per-row rounding helpers of the CUDA library
 // (common.cuh): pred_recip_fast must equal floor(z * 2^64 / f) computed by
 // 128-bit division, and pred_fixed must equal ceil(v * z / f), on random and
-// edge operands.  Built by nvcc as host code only; prints "ok N" or the first
+// edge operands; so must pred_fast with pred_recip_any (the 32-bit reciprocal
+// floor(z * 2^32 / f) when f < 2^32).  Built by nvcc as host code only; prints "ok N" or the first
 // mismatch and exits non-zero.
 #include <cstdio>
 #include <cstdint>
@@ -33,6 +34,15 @@ static int check(uint64_t z, uint64_t f, uint32_t v) {
            (unsigned long long)want);
     return 1;
   }
+  // the path the prediction kernel takes: 32-bit reciprocal when f < 2^32
+  const uint64_t Ra = spg::pred_recip_any(z, f);
+  const uint64_t Rw = f < (1ull << 32) ? (uint64_t)(((u128)z << 32) / f) : Rx;
+  const int got2 = spg::pred_fast(v, z, f, Ra);
+  if (Ra != Rw || (uint64_t)got2 != want) {
+    printf("fast-path mismatch v=%u z=%llu f=%llu R %llu (want %llu) got %d want %llu\n", v, (unsigned long long)z,
+           (unsigned long long)f, (unsigned long long)Ra, (unsigned long long)Rw, got2, (unsigned long long)want);
+    return 1;
+  }
   return 0;
 }
 
@@ -59,6 +69,16 @@ int main() {
     if (f < 2) f = 2;
     const uint64_t z = next64() % f;
     const uint32_t v = (uint32_t)(next64() >> 33);
+    if (check(z, f, v)) return 1;
+    ++n;
+  }
+  // the 32-bit path: f < 2^32, large v, z near f
+  for (int i = 0; i < 1000000; ++i) {
+    const int bits = 1 + (int)(next64() % 32);
+    uint64_t f = next64() >> (64 - bits);
+    if (f < 2) f = 2;
+    const uint64_t z = (i & 1) ? f - 1 - next64() % (f < 64 ? f : 64) : next64() % f;
+    const uint32_t v = (i & 2) ? 2147483647u - (uint32_t)(next64() % 1024) : (uint32_t)(next64() >> 33);
     if (check(z, f, v)) return 1;
     ++n;
   }

@@ -139,6 +139,24 @@ def test_empty_and_degenerate_matrices():
         assert_prediction_equal(g, oracle_predict(one, B, oracle.BERNOULLI, 0, T), f"single row T={T}")
 
 
+@pytest.mark.parametrize("rows", [(1 << 20) - 3, (1 << 21) + 12345, 3 << 20])
+def test_tall_sparse_many_rows_per_block(rows):
+    # about one nonzero per row: each block of the prediction holds from about
+    # 8 thousand to over 20 thousand rows, i.e. one to six 4096-row chunks in
+    # the per-block scan (scanned before or after the wait on the blocks
+    # before it), with ragged ends
+    A = W.erdos_renyi(rows, 1, 41 + rows % 7, ncols=1 << 15)
+    B = W.erdos_renyi(1 << 15, 3, 42, ncols=5000)
+    dA, dB = to_dev(A), to_dev(B)
+    ws = sp.Workspace.for_operands(dA, dB)
+    for ref in (False, True):
+        for seed, ratio in ((5, 0.01), (6, 0.3)):
+            T = int(ratio * TWO32)
+            g = gpu_predict(A, B, sp.SAMPLE_BERNOULLI, seed, T, reference=ref, ws=ws, dA=dA, dB=dB)
+            o = oracle_predict(A, B, oracle.BERNOULLI, seed, T, reference=ref)
+            assert_prediction_equal(g, o, f"rows {rows} ref {ref} seed {seed}")
+
+
 def test_empty_sample_and_full_sample():
     A = W.erdos_renyi(5000, 9, 5)
     for T in (0, TWO32):
