@@ -51,6 +51,8 @@ def _bind(path):
         fn.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _i64, _p, _p, _p, _p]
     lib.orc_symbolic_exact.restype = _i64
     lib.orc_symbolic_exact.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _p]
+    lib.orc_spgemm_numeric.restype = _i64
+    lib.orc_spgemm_numeric.argtypes = [_i64, _i64] + [_p] * 11
     lib.orc_num_threads.restype = ctypes.c_int
     lib.orc_set_num_threads.argtypes = [ctypes.c_int]
     return lib
@@ -210,6 +212,32 @@ def symbolic_exact(A, B):
     if Z < 0:
         raise MemoryError("oracle marker allocation failed")
     return nnz, offsets, int(Z)
+
+
+def numeric(A, a_val, B, b_val):
+    """C = A*B with values (the numeric phase the prediction allocates for):
+    returns (offsets int64[M+1], col int32, val float64, abs_sum float64,
+    terms int32), columns ascending within each row; abs_sum and terms are the
+    sum of |products| and the number of products behind each entry."""
+    if A.cols != B.rows:
+        raise ValueError("A.cols != B.rows")
+    a_rpt, a_col = _csr(A)
+    b_rpt, b_col = _csr(B)
+    a_val = np.ascontiguousarray(a_val, dtype=np.float32)
+    b_val = np.ascontiguousarray(b_val, dtype=np.float32)
+    if a_val.shape[0] != a_col.shape[0] or b_val.shape[0] != b_col.shape[0]:
+        raise ValueError("one value per nonzero")
+    _, offsets, Z = symbolic_exact(A, B)
+    col = np.zeros(Z, dtype=np.int32)
+    val = np.zeros(Z, dtype=np.float64)
+    abs_sum = np.zeros(Z, dtype=np.float64)
+    terms = np.zeros(Z, dtype=np.int32)
+    n = _load().orc_spgemm_numeric(A.rows, B.cols, _ptr(a_rpt), _ptr(a_col), _ptr(a_val), _ptr(b_rpt),
+                                   _ptr(b_col), _ptr(b_val), _ptr(offsets), _ptr(col), _ptr(val),
+                                   _ptr(abs_sum), _ptr(terms))
+    if n < 0:
+        raise MemoryError("oracle accumulator allocation failed")
+    return offsets, col, val, abs_sum, terms
 
 
 def estimates(F, Z, f, z, M, S):

@@ -278,6 +278,85 @@ int64_t orc_symbolic_exact(int64_t M, int64_t N, const int32_t* a_rpt, const int
   return Z;
 }
 
+/* ---------------------------------------------------------------------------
+ * Numeric product C = A*B: the numeric phase that the predicted structure
+ * allocates memory for (Sec. I; the consumer of the prediction, outside the
+ * paper's own experiments).  Row i of C holds every column reached by a
+ * product of A's row i with the rows of B, with the value sum_k a_ik * b_kc.
+ * Textbook row-wise (Gustavson) product with a dense accumulator: each product
+ * is formed in double precision from the single-precision inputs (exact: 24-bit
+ * by 24-bit mantissas), summed in double, and the row's columns are written in
+ * ascending order.  For every entry it also writes the sum of |a_ik * b_kc| and
+ * the number of products, which bound the rounding of a single-precision sum.
+ * c_rpt holds the exact offsets (orc_symbolic_exact).  Returns the number of
+ * entries written, or -1 when the accumulator could not be allocated.
+ * ------------------------------------------------------------------------- */
+static int orc_cmp_i32(const void* x, const void* y) {
+  const int32_t a = *(const int32_t*)x, b = *(const int32_t*)y;
+  return (a > b) - (a < b);
+}
+
+int64_t orc_spgemm_numeric(int64_t M, int64_t N, const int32_t* a_rpt, const int32_t* a_col,
+                           const float* a_val, const int32_t* b_rpt, const int32_t* b_col,
+                           const float* b_val, const int64_t* c_rpt, int32_t* c_col, double* c_val,
+                           double* c_abs, int32_t* c_terms) {
+  int64_t total = 0;
+  int failed = 0;
+#pragma omp parallel reduction(+ : total) reduction(| : failed)
+  {
+    const size_t n_alloc = (size_t)(N > 0 ? N : 1);
+    double* acc = (double*)malloc(n_alloc * sizeof(double));
+    double* acc_abs = (double*)malloc(n_alloc * sizeof(double));
+    int32_t* terms = (int32_t*)malloc(n_alloc * sizeof(int32_t));
+    int64_t* mark = (int64_t*)malloc(n_alloc * sizeof(int64_t));
+    int32_t* list = (int32_t*)malloc(n_alloc * sizeof(int32_t));
+    if (!acc || !acc_abs || !terms || !mark || !list) {
+      failed = 1;
+    } else {
+      for (int64_t c = 0; c < N; ++c) mark[c] = -1;
+      int64_t i;
+#pragma omp for schedule(static)
+      for (i = 0; i < M; ++i) {
+        int64_t n = 0;
+        for (int64_t j = a_rpt[i]; j < a_rpt[i + 1]; ++j) {
+          const int32_t k = a_col[j];
+          const double a = (double)a_val[j];
+          for (int64_t t = b_rpt[k]; t < b_rpt[k + 1]; ++t) {
+            const int32_t c = b_col[t];
+            const double prod = a * (double)b_val[t];
+            if (mark[c] != i) {
+              mark[c] = i;
+              acc[c] = 0.0;
+              acc_abs[c] = 0.0;
+              terms[c] = 0;
+              list[n++] = c;
+            }
+            acc[c] += prod;
+            acc_abs[c] += prod < 0.0 ? -prod : prod;
+            terms[c] += 1;
+          }
+        }
+        qsort(list, (size_t)n, sizeof(int32_t), orc_cmp_i32);
+        const int64_t o = c_rpt[i];
+        for (int64_t q = 0; q < n; ++q) {
+          const int32_t c = list[q];
+          c_col[o + q] = c;
+          c_val[o + q] = acc[c];
+          c_abs[o + q] = acc_abs[c];
+          c_terms[o + q] = terms[c];
+        }
+        total += n;
+      }
+    }
+    free(acc);
+    free(acc_abs);
+    free(terms);
+    free(mark);
+    free(list);
+  }
+  return failed ? -1 : total;
+}
+
 /* Number of OpenMP threads a parallel region uses (1 without OpenMP). */
 int orc_num_threads(void) {
 #ifdef _OPENMP

@@ -34,6 +34,11 @@ MUTANTS = {
     "scan subtracts": ("(u128)(uint64_t)f);\n    pred[i] = p;\n    offsets[i + 1] = offsets[i] + p;",
                        "(u128)(uint64_t)f);\n    pred[i] = p;\n    offsets[i + 1] = offsets[i] - p;"),
     "empty sample not flagged": ("if (f == 0) status |= ORC_WARN_EMPTY_SAMPLE;", ""),
+    "numeric overwrites the sum": ("            acc[c] += prod;", "            acc[c] = prod;"),
+    "numeric squares A's value": ("const double prod = a * (double)b_val[t];", "const double prod = a * a;"),
+    "numeric counts each column once": ("            terms[c] += 1;", "            terms[c] = 1;"),
+    "numeric leaves rows unsorted": ("        qsort(list, (size_t)n, sizeof(int32_t), orc_cmp_i32);\n", ""),
+    "numeric |.| keeps the sign": ("acc_abs[c] += prod < 0.0 ? -prod : prod;", "acc_abs[c] += prod;"),
     "sampled flop uses first row": ("for (int64_t r = 0; r < n_ids; ++r) f += flop[ids[r]];\n  int64_t status = 0;\n  if (f == 0)",
                                     "for (int64_t r = 0; r < n_ids; ++r) f += flop[ids[0]];\n  int64_t status = 0;\n  if (f == 0)"),
 }
@@ -52,6 +57,9 @@ def _pins():
     for name in ("lap64", "er", "rmat", "rect"):
         yield lambda n=name: P.test_prediction_invariants(n, oracle.BERNOULLI)
         yield lambda n=name: P.test_prediction_invariants(n, oracle.PAPER_DRAW)
+    yield lambda: P.test_numeric_against_dense_product((17, 33, 9), 0.5)
+    yield lambda: P.test_numeric_laplacian_squared_closed_form(8)
+    yield P.test_numeric_sum_identity
     yield P.test_empty_sample_falls_back_to_flop
     yield P.test_paper_draw_counts_repeats
 

@@ -322,3 +322,76 @@ def test_rectangular_reshape_rule():
     dB[np.repeat(np.arange(300), np.diff(B.rpt)), B.col] = 1
     ref = np.count_nonzero(dA[:, :120] @ dB[:120, :], axis=1)
     assert np.array_equal(oracle.row_nnz(A2, B2), ref)
+
+
+# ---------------------------------------------------------------- numeric product
+def _signed_values(m, seed):
+    """Seeded single-precision values in [-1, 1) for every nonzero (cancellation possible)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, m.nnz).astype(np.float32)
+
+
+def _dense(m, val):
+    d = np.zeros((m.rows, m.cols), dtype=np.float64)
+    rows = np.repeat(np.arange(m.rows), np.diff(m.rpt))
+    d[rows, m.col] = val.astype(np.float64)
+    return d
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (5, 3, 7), (17, 33, 9), (40, 64, 64)])
+@pytest.mark.parametrize("density", [0.1, 0.5])
+def test_numeric_against_dense_product(shape, density):
+    M, K, N = shape
+    A, B, da, db = W.tiny_random(M, K, N, density, seed=M * 7 + K * 3 + N)
+    av, bv = _signed_values(A, 1), _signed_values(B, 2)
+    Ad, Bd = _dense(A, av), _dense(B, bv)
+    offs, col, val, abs_sum, terms = oracle.numeric(A, av, B, bv)
+    # structure: the boolean product (no cancellation in a count of paths)
+    paths = da.astype(np.int64) @ db.astype(np.int64)
+    assert np.array_equal(np.diff(offs), np.count_nonzero(paths, axis=1))
+    rows = np.repeat(np.arange(M), np.diff(offs))
+    assert np.array_equal(paths[rows, col], terms)
+    for i in range(M):  # ascending columns within each row
+        assert np.all(np.diff(col[offs[i]:offs[i + 1]]) > 0)
+    # values: the dense double product (products of single-precision values are exact in double)
+    ref = Ad @ Bd
+    np.testing.assert_allclose(val, ref[rows, col], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(abs_sum, (np.abs(Ad) @ np.abs(Bd))[rows, col], rtol=1e-12, atol=1e-12)
+    # and nothing outside the structure
+    mask = np.zeros((M, N), dtype=bool)
+    mask[rows, col] = True
+    assert np.all(ref[~mask] == 0.0)
+
+
+@pytest.mark.parametrize("N", [5, 8, 13])
+def test_numeric_laplacian_squared_closed_form(N):
+    # A = 4 I - (sum of the four grid shifts), Dirichlet: (A^2)_ij by geometry:
+    # i = j: 16 + deg(i); one step apart: -8; diagonal neighbours: 2 (two paths);
+    # two steps in a line: 1 (one path through the middle node)
+    A = W.laplacian_2d(N, values="laplace")
+    av = A.val.astype(np.float32)
+    offs, col, val, _, _ = oracle.numeric(A, av, A, av)
+    for i in range(N * N):
+        x, y = i % N, i // N
+        deg = sum(1 for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)) if 0 <= x + dx < N and 0 <= y + dy < N)
+        want = {i: 16.0 + deg}
+        for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            if 0 <= x + dx < N and 0 <= y + dy < N:
+                want[(x + dx) + N * (y + dy)] = -8.0
+            if 0 <= x + 2 * dx < N and 0 <= y + 2 * dy < N:
+                want[(x + 2 * dx) + N * (y + 2 * dy)] = 1.0
+        for dx, dy in ((1, 1), (1, -1), (-1, 1), (-1, -1)):
+            if 0 <= x + dx < N and 0 <= y + dy < N:
+                want[(x + dx) + N * (y + dy)] = 2.0
+        got = dict(zip(col[offs[i]:offs[i + 1]].tolist(), val[offs[i]:offs[i + 1]].tolist()))
+        assert got == want, (i, got, want)
+
+
+def test_numeric_sum_identity():
+    # sum of all entries of A*B = sum_k (column sum k of A) * (row sum k of B)
+    A = W.erdos_renyi(300, 6, 21, ncols=200)
+    B = W.erdos_renyi(200, 5, 22, ncols=250)
+    av, bv = _signed_values(A, 3), _signed_values(B, 4)
+    _, _, val, _, _ = oracle.numeric(A, av, B, bv)
+    colsum_a = np.bincount(A.col, weights=av.astype(np.float64), minlength=A.cols)
+    rowsum_b = np.add.reduceat(bv.astype(np.float64), B.rpt[:-1]) * (np.diff(B.rpt) > 0)
+    assert math.isclose(val.sum(), float(colsum_a @ rowsum_b), rel_tol=1e-9, abs_tol=1e-9)
