@@ -133,6 +133,11 @@ def load():
         fn.restype = ctypes.c_int
     lib.spgemm_status_string.restype = ctypes.c_char_p
     lib.spgemm_status_string.argtypes = [ctypes.c_int]
+    i64 = ctypes.c_int64
+    lib.spgemm_numeric_into.argtypes = [C, P, C, P, P, P, P, i64, P, P, P, sz, P]
+    lib.spgemm_numeric_compact.argtypes = [C, P, C, P, P, P, P, i64, P, P, P, P, i64, P, P, sz, P]
+    lib.spgemm_numeric_into.restype = ctypes.c_int
+    lib.spgemm_numeric_compact.restype = ctypes.c_int
     for fn in (lib.spgemm_flop_per_row, lib.spgemm_predict_cr, lib.spgemm_predict_structure,
                lib.spgemm_predict_reference, lib.spgemm_symbolic_exact, lib.spgemm_sample_rows,
                lib.spgemm_validate_csr):
@@ -234,6 +239,21 @@ def read_result(res):
                 status=status)
 
 
+NUMERIC_RESULT_BYTES = 40
+
+
+def new_numeric_result(device="cuda"):
+    torch = _torch()
+    return torch.zeros(NUMERIC_RESULT_BYTES // 8, dtype=torch.int64, device=device)
+
+
+def read_numeric_result(res):
+    """Host copy of a device numeric result record as a dict."""
+    v = res.cpu().tolist()
+    return dict(nnz_total=v[0], overflow_rows=v[1], overflow_nnz=v[2], alloc_total=v[3],
+                status=v[4] & 0xFFFFFFFF)
+
+
 # ---- the C ABI, same names and argument order -----------------------------------
 def spgemm_flop_per_row(A, B, flop_row, res, ws, stream=None):
     a, b = A.struct(), B.struct()
@@ -294,6 +314,31 @@ def spgemm_set_profile_events(before, after):
     b = None if before is None else ctypes.c_void_p(before.cuda_event)
     a = None if after is None else ctypes.c_void_p(after.cuda_event)
     return load().spgemm_set_profile_events(b, a)
+
+
+def _numel(t):
+    return 0 if t is None else int(t.numel())
+
+
+def spgemm_numeric_into(A, a_val, B, b_val, alloc_offsets, c_col, c_val, nnz_row, res, ws, stream=None):
+    """C = A*B into the allocation layout alloc_offsets (see include/spgemm_predict.h)."""
+    a, b = A.struct(), B.struct()
+    cap = min(_numel(c_col), _numel(c_val))
+    return load().spgemm_numeric_into(ctypes.byref(a), _ptr(a_val), ctypes.byref(b), _ptr(b_val),
+                                      _ptr(alloc_offsets), _ptr(c_col), _ptr(c_val), cap, _ptr(nnz_row),
+                                      _ptr(res), ws.ptr(), ws.nbytes, _stream(stream))
+
+
+def spgemm_numeric_compact(A, a_val, B, b_val, alloc_offsets, c_col, c_val, nnz_row, out_rpt, out_col,
+                           out_val, res, ws, stream=None):
+    """The exact CSR of C from spgemm_numeric_into's output."""
+    a, b = A.struct(), B.struct()
+    cap = min(_numel(c_col), _numel(c_val))
+    out_cap = min(_numel(out_col), _numel(out_val))
+    return load().spgemm_numeric_compact(ctypes.byref(a), _ptr(a_val), ctypes.byref(b), _ptr(b_val),
+                                         _ptr(alloc_offsets), _ptr(c_col), _ptr(c_val), cap, _ptr(nnz_row),
+                                         _ptr(out_rpt), _ptr(out_col), _ptr(out_val), out_cap, _ptr(res),
+                                         ws.ptr(), ws.nbytes, _stream(stream))
 
 
 def spgemm_status_string(code):
@@ -479,3 +524,44 @@ class Batch:
         pred, offs, flop = self.outputs[i]
         return Prediction(pred, offs, flop, self.res[i])
 
+
+
+# ---- the consumer: numeric product allocated by the prediction ------------------
+@dataclass
+class NumericProduct:
+    rpt: "object"      # int64[M + 1] exact offsets (device)
+    col: "object"      # int32[NNZ(C)] (device; column order within a row is free)
+    val: "object"      # float32[NNZ(C)] (device)
+    info: dict         # prediction and numeric result records, allocation sizes
+
+
+def numeric_product(A, a_val, B, b_val, cfg, ws=None, stream=None, compact=True):
+    """C = A*B the way the prediction is meant to be used: predict the structure,
+    allocate C by the predicted offsets, compute every row into that allocation,
+    then build the exact CSR (rows that fitted are moved, rows that overflowed are
+    computed again).  One host read of the numeric result sizes the exact arrays.
+    With compact=False, returns the padded layout (rpt = the predicted offsets,
+    valid only when no row overflowed) without the compaction."""
+    torch = _torch()
+    dev = A.rpt.device
+    ws = ws or Workspace.for_operands(A, B)
+    pred = predict_structure(A, B, cfg, ws=ws, stream=stream)
+    presult = read_result(pred.res)
+    alloc = max(presult["pred_total"], 0)
+    c_col = torch.empty(max(alloc, 1), dtype=torch.int32, device=dev)[:alloc]
+    c_val = torch.empty(max(alloc, 1), dtype=torch.float32, device=dev)[:alloc]
+    nnz_row = torch.empty(max(A.rows, 0), dtype=torch.int32, device=dev)
+    nres = new_numeric_result(dev)
+    _check(spgemm_numeric_into(A, a_val, B, b_val, pred.offsets, c_col, c_val, nnz_row, nres, ws, stream),
+           "spgemm_numeric_into")
+    info = {"prediction": presult, "numeric": read_numeric_result(nres)}
+    if not compact:
+        return NumericProduct(pred.offsets, c_col, c_val, info)
+    Z = info["numeric"]["nnz_total"]
+    out_rpt = torch.empty(A.rows + 1, dtype=torch.int64, device=dev)
+    out_col = torch.empty(max(Z, 1), dtype=torch.int32, device=dev)[:Z]
+    out_val = torch.empty(max(Z, 1), dtype=torch.float32, device=dev)[:Z]
+    _check(spgemm_numeric_compact(A, a_val, B, b_val, pred.offsets, c_col, c_val, nnz_row, out_rpt, out_col,
+                                  out_val, nres, ws, stream), "spgemm_numeric_compact")
+    info["numeric"]["status"] = read_numeric_result(nres)["status"]
+    return NumericProduct(out_rpt, out_col, out_val, info)

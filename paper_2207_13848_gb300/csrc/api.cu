@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "k_batch.cuh"
+#include "k_numeric.cuh"
 #include "k_dedup.cuh"
 #include "k_flop.cuh"
 #include "k_predict.cuh"
@@ -44,6 +45,8 @@ struct DeviceLimits {
   // single-launch predictor
   int pred_blocks_per_sm = 0;
   int pred_dyn_smem = 0;
+  // numeric product (the consumer)
+  int num_blocks_per_sm = 0;
   bool ok = false;
 };
 
@@ -113,7 +116,12 @@ void init_limits(int dev, DeviceLimits* L) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_predict<kModeReference>, kPredThreads, pdyn) != cudaSuccess) return;
   L->pred_blocks_per_sm = min(b, b2);
   L->pred_dyn_smem = pdyn;
-  L->ok = L->pred_blocks_per_sm > 0 && L->flop_blocks_per_sm > 0 && L->scan_blocks_per_sm > 0 && L->dedup_blocks_per_sm > 0 &&
+  // numeric product
+  if (cudaFuncSetAttribute(k_numeric_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNumRowsSmem) != cudaSuccess) return;
+  if (cudaFuncSetAttribute(k_numeric_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNumHeavySmem) != cudaSuccess) return;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_numeric_rows, kNumThreads, kNumRowsSmem) != cudaSuccess) return;
+  L->num_blocks_per_sm = b;
+  L->ok = L->pred_blocks_per_sm > 0 && L->num_blocks_per_sm > 0 && L->flop_blocks_per_sm > 0 && L->scan_blocks_per_sm > 0 && L->dedup_blocks_per_sm > 0 &&
           L->kb_flop_blocks_per_sm > 0 && L->kb_sample_blocks_per_sm[0] > 0 &&
           L->kb_sample_blocks_per_sm[1] > 0 && L->kb_sample_blocks_per_sm[2] > 0;
 }
@@ -249,11 +257,11 @@ int launch_flop(const DeviceLimits* L, const FlopArgs& f, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 
-template <class Src, bool SYM>
-int launch_scan(const DeviceLimits* L, const Src& src, long long n, const Workspace& w,
-                spgemm_result_t* res, cudaStream_t st) {
+template <class Src, bool SYM, class Res = spgemm_result_t>
+int launch_scan(const DeviceLimits* L, const Src& src, long long n, const Workspace& w, Res* res,
+                cudaStream_t st) {
   const int g = grid_for(n, (long long)kScanThreads * kScanRows * 2, (long long)L->sms * L->scan_blocks_per_sm);
-  k_scan_rows<Src, SYM><<<g, kScanThreads, 0, st>>>(src, n, w, res);
+  k_scan_rows<Src, SYM, Res><<<g, kScanThreads, 0, st>>>(src, n, w, res);
   return cudaGetLastError() == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 
@@ -589,6 +597,65 @@ int batch_prepare(const spgemm_batch_item_t* items, int n, const spgemm_batch_tu
   return SPGEMM_OK;
 }
 
+// ---- numeric product into a given allocation (the consumer of the prediction)
+
+int numeric_check(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t* B, const float* b_val,
+                  const int64_t* alloc, const void* c_col, const void* c_val, int64_t c_capacity,
+                  const int32_t* nnz_row, const spgemm_numeric_result_t* res, void* ws, size_t ws_bytes) {
+  if (!csr_ok(A) || !csr_ok(B) || !res || !ws || !alloc) return SPGEMM_ERR_INVALID_ARG;
+  if ((A->nnz > 0 && !a_val) || (B->nnz > 0 && !b_val) || (A->rows > 0 && !nnz_row)) return SPGEMM_ERR_INVALID_ARG;
+  if (c_capacity < 0 || (c_capacity > 0 && (!c_col || !c_val))) return SPGEMM_ERR_INVALID_ARG;
+  if (A->cols != B->rows) return SPGEMM_ERR_DIM_MISMATCH;
+  if (!csr_fits(A) || !csr_fits(B)) return SPGEMM_ERR_TOO_LARGE;
+  if (ws_bytes < ws_bytes_for(A->rows, A->cols)) return SPGEMM_ERR_WORKSPACE;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return SPGEMM_ERR_WORKSPACE;
+  return SPGEMM_OK;
+}
+
+NumArgs numeric_args(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t* B, const float* b_val,
+                     const int64_t* alloc, int32_t* c_col, float* c_val, int64_t c_capacity, int32_t* nnz_row,
+                     spgemm_numeric_result_t* res, const Workspace& w) {
+  NumArgs a;
+  a.M = A->rows;
+  a.K = B->rows;
+  a.N = B->cols;
+  a.nnzA = A->nnz;
+  a.nnzB = B->nnz;
+  a.a_rpt = A->rpt;
+  a.a_col = A->col;
+  a.a_val = a_val;
+  a.b_rpt = B->rpt;
+  a.b_col = B->col;
+  a.b_val = b_val;
+  a.alloc = reinterpret_cast<const long long*>(alloc);
+  a.c_col = c_col;
+  a.c_val = c_val;
+  a.alloc_cap = c_capacity;
+  a.nnz_row = nnz_row;
+  a.out_rpt = nullptr;
+  a.out_col = nullptr;
+  a.out_val = nullptr;
+  a.out_cap = 0;
+  a.mode = kNumInto;
+  a.heavy_count = &w.hdr->heavy_count;
+  a.heavy = w.heavy;
+  a.heavy_cap = A->rows;
+  a.status = &w.hdr->status;
+  a.res = res;
+  return a;
+}
+
+// Warp-per-row pass, block-per-row pass over the rows it queued, finish.
+int launch_numeric(const DeviceLimits* L, const NumArgs& a, cudaStream_t st) {
+  if (a.M > 0) {
+    const int g = grid_for(a.M, kNumWarps, (long long)L->sms * L->num_blocks_per_sm);
+    k_numeric_rows<<<g, kNumThreads, kNumRowsSmem, st>>>(a);
+    k_numeric_heavy<<<L->sms, kNumHeavyThreads, kNumHeavySmem, st>>>(a);
+  }
+  k_numeric_finish<<<1, 1, 0, st>>>(a, a.status);
+  return cudaGetLastError() == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -660,6 +727,46 @@ int spgemm_symbolic_exact(const spgemm_csr_t* A, const spgemm_csr_t* B, int32_t*
   if ((rc = launch_dedup(L, d, st))) return rc;
   ScanNnz src{nnz_row, reinterpret_cast<long long*>(offsets)};
   return launch_scan<ScanNnz, true>(L, src, A->rows, w, res, st);
+}
+
+int spgemm_numeric_into(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t* B,
+                        const float* b_val, const int64_t* alloc_offsets, int32_t* c_col,
+                        float* c_val, int64_t c_capacity, int32_t* nnz_row,
+                        spgemm_numeric_result_t* res, void* ws, size_t ws_bytes, void* stream) {
+  int rc = numeric_check(A, a_val, B, b_val, alloc_offsets, c_col, c_val, c_capacity, nnz_row, res, ws, ws_bytes);
+  if (rc) return rc;
+  const DeviceLimits* L = limits();
+  if (!L) return SPGEMM_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Workspace w = ws_carve(ws, A->rows);
+  if (cudaMemsetAsync(res, 0, sizeof(*res), st) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  const NumArgs a = numeric_args(A, a_val, B, b_val, alloc_offsets, c_col, c_val, c_capacity, nnz_row, res, w);
+  return launch_numeric(L, a, st);
+}
+
+int spgemm_numeric_compact(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t* B,
+                           const float* b_val, const int64_t* alloc_offsets, const int32_t* c_col,
+                           const float* c_val, int64_t c_capacity, const int32_t* nnz_row,
+                           int64_t* out_rpt, int32_t* out_col, float* out_val, int64_t out_capacity,
+                           spgemm_numeric_result_t* res, void* ws, size_t ws_bytes, void* stream) {
+  int rc = numeric_check(A, a_val, B, b_val, alloc_offsets, c_col, c_val, c_capacity, nnz_row, res, ws, ws_bytes);
+  if (rc) return rc;
+  if (!out_rpt || out_capacity < 0 || (out_capacity > 0 && (!out_col || !out_val))) return SPGEMM_ERR_INVALID_ARG;
+  const DeviceLimits* L = limits();
+  if (!L) return SPGEMM_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Workspace w = ws_carve(ws, A->rows);
+  // the rows that fitted are only read here
+  NumArgs a = numeric_args(A, a_val, B, b_val, alloc_offsets, const_cast<int32_t*>(c_col),
+                           const_cast<float*>(c_val), c_capacity, const_cast<int32_t*>(nnz_row), res, w);
+  a.mode = kNumCompact;
+  a.out_rpt = reinterpret_cast<const long long*>(out_rpt);
+  a.out_col = out_col;
+  a.out_val = out_val;
+  a.out_cap = out_capacity;
+  ScanNumNnz src{nnz_row, reinterpret_cast<long long*>(out_rpt)};
+  if ((rc = launch_scan<ScanNumNnz, false, spgemm_numeric_result_t>(L, src, A->rows, w, res, st))) return rc;
+  return launch_numeric(L, a, st);
 }
 
 int spgemm_sample_rows(int64_t rows, const spgemm_config_t* cfg, int32_t* ids, int64_t capacity,

@@ -3,6 +3,8 @@
 // and the finalisation of the sampling-only call.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace spg {
@@ -20,6 +22,16 @@ struct ScanNnz {
     offsets[n] = total;
     res->pred_total = total;
   }
+};
+
+// Values: exact nnz per row of a numeric product; output: the exact CSR's
+// offsets (M + 1 entries).  The result record keeps its fields.
+struct ScanNumNnz {
+  const int* vals;
+  long long* offsets;
+  __device__ int value(long long r) const { return vals[r]; }
+  __device__ void emit(long long r, long long excl, int) const { offsets[r] = excl; }
+  __device__ void finish(long long n, long long total, spgemm_numeric_result_t*) const { offsets[n] = total; }
 };
 
 // Values: 1 if the candidate is in the sample; output: its row id at position excl.
@@ -49,10 +61,10 @@ struct ScanSample {
 // sums of blocks 0..c-1 (bounded waits) and writes the exclusive prefixes.
 // The last block to finish copies the workspace accumulators into *res
 // (flop_total = flop_s = f_acc, nnz_s = z_acc, n_sampled = s_acc unless the
-// source writes it) and resets them.
-template <class Src, bool SYMBOLIC>
-__global__ void __launch_bounds__(kScanThreads) k_scan_rows(Src src, long long n, Workspace ws,
-                                                           spgemm_result_t* res) {
+// source writes it) and resets them; a numeric result record only gains the
+// status bits.
+template <class Src, bool SYMBOLIC, class Res = spgemm_result_t>
+__global__ void __launch_bounds__(kScanThreads) k_scan_rows(Src src, long long n, Workspace ws, Res* res) {
   __shared__ long long red[kScanThreads / 32 + 1];
   const int t = threadIdx.x, G = gridDim.x, c = blockIdx.x;
   WsHeader* hdr = ws.hdr;
@@ -95,18 +107,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_rows(Src src, long long n
     if (atomicAdd(&hdr->done, 1u) == (unsigned)G - 1) {
       __threadfence();
       volatile WsHeader* vh = hdr;
-      if (SYMBOLIC) {
-        res->flop_total = (long long)vh->f_acc;
-        res->flop_s = (long long)vh->f_acc;
-        res->nnz_s = (long long)vh->z_acc;
-        res->n_sampled = (long long)vh->s_acc;
+      if constexpr (std::is_same<Res, spgemm_result_t>::value) {
+        if (SYMBOLIC) {
+          res->flop_total = (long long)vh->f_acc;
+          res->flop_s = (long long)vh->f_acc;
+          res->nnz_s = (long long)vh->z_acc;
+          res->n_sampled = (long long)vh->s_acc;
+        } else {
+          res->flop_total = 0;
+          res->flop_s = 0;
+          res->nnz_s = 0;
+          res->pred_total = 0;
+        }
+        res->status = (int)vh->status;
       } else {
-        res->flop_total = 0;
-        res->flop_s = 0;
-        res->nnz_s = 0;
-        res->pred_total = 0;
+        res->status |= (int)vh->status;
       }
-      res->status = (int)vh->status;
       vh->f_acc = 0;
       vh->z_acc = 0;
       vh->s_acc = 0;
