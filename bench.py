@@ -559,6 +559,129 @@ def run_accuracy(args):
     return 0
 
 
+def run_numeric(args):
+    """The consumer of the prediction: the numeric product C = A*B with C
+    allocated by the predicted offsets (prediction + numeric pass + compaction to
+    the exact CSR) against the precise two-phase method (exact symbolic phase +
+    numeric pass into the exact offsets), on the ER bench matrix with fp32
+    values and on R-MAT scale 16 (rows overflow there).  L2 flushed before every
+    step; CUDA events; device-resident inputs."""
+    import torch
+    import paper_2207_13848_gb300 as sp
+    from paper_2207_13848_gb300 import build as spbuild
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spbuild.build()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 18, dtype=torch.int32, device=dev)
+    peak, peak_src = measured_peaks()
+    workloads_ = [
+        ("ER n=2^20, Poisson(16) nnz/row, C=A*A, fp32 U(0,1) values, 1% Bernoulli",
+         W.erdos_renyi(1 << 20, 16, 2000, values=True), threshold()),
+        ("R-MAT scale 16, edge factor 16, C=A*A, fp32 U(0,1) values, 0.5% Bernoulli",
+         W.rmat(16, 16, seed=3000, values=True), int(0.005 * TWO32)),
+    ]
+    out = []
+    K = max(3, min(args.steps, 20))
+    for name, A, T in workloads_:
+        dA = sp.DeviceCSR.from_host(A, dev)
+        val = torch.from_numpy(np.asarray(A.val, dtype=np.float32)).to(dev)
+        ws = sp.Workspace.for_operands(dA, dA, dev)
+        cfg = sp.config(threshold=T, seed=0)
+        M = A.rows
+        # sizes from one untimed run
+        ex = sp.symbolic_exact(dA, dA, ws=ws)
+        Z = sp.read_result(ex.res)["pred_total"]
+        pr = sp.predict_structure(dA, dA, cfg, ws=ws, want_flop=True)
+        presult = sp.read_result(pr.res)
+        alloc = presult["pred_total"]
+        F = presult["flop_total"]
+        nnz_row = torch.empty(M, dtype=torch.int32, device=dev)
+        nres = sp.new_numeric_result(dev)
+        c_col = torch.empty(max(alloc, Z, 1), dtype=torch.int32, device=dev)
+        c_val = torch.empty(max(alloc, Z, 1), dtype=torch.float32, device=dev)
+        o_rpt = torch.empty(M + 1, dtype=torch.int64, device=dev)
+        o_col = torch.empty(max(Z, 1), dtype=torch.int32, device=dev)[:Z]
+        o_val = torch.empty(max(Z, 1), dtype=torch.float32, device=dev)[:Z]
+        pad_col, pad_val = c_col[:alloc], c_val[:alloc]
+        exa_col, exa_val = c_col[:Z], c_val[:Z]
+
+        def precise():
+            r1 = sp.spgemm_symbolic_exact(dA, dA, ex.pred, ex.offsets, ex.res, ws, stream)
+            r2 = sp.spgemm_numeric_into(dA, val, dA, val, ex.offsets, exa_col, exa_val, nnz_row, nres, ws, stream)
+            if r1 or r2:
+                raise RuntimeError("precise method failed")
+
+        def predicted():
+            r1 = sp.spgemm_predict_structure(dA, dA, cfg, pr.pred, pr.offsets, None, pr.res, ws, stream)
+            r2 = sp.spgemm_numeric_into(dA, val, dA, val, pr.offsets, pad_col, pad_val, nnz_row, nres, ws, stream)
+            r3 = sp.spgemm_numeric_compact(dA, val, dA, val, pr.offsets, pad_col, pad_val, nnz_row, o_rpt, o_col,
+                                           o_val, nres, ws, stream)
+            if r1 or r2 or r3:
+                raise RuntimeError("predicted allocation failed")
+
+        def predicted_padded():
+            r1 = sp.spgemm_predict_structure(dA, dA, cfg, pr.pred, pr.offsets, None, pr.res, ws, stream)
+            r2 = sp.spgemm_numeric_into(dA, val, dA, val, pr.offsets, pad_col, pad_val, nnz_row, nres, ws, stream)
+            if r1 or r2:
+                raise RuntimeError("predicted allocation failed")
+
+        def numeric_only():
+            if sp.spgemm_numeric_into(dA, val, dA, val, pr.offsets, pad_col, pad_val, nnz_row, nres, ws, stream):
+                raise RuntimeError("numeric pass failed")
+
+        def timed(fn):
+            for _ in range(3):
+                flush.fill_(1)
+                fn()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            for k, (a, b) in enumerate(ev):
+                flush.fill_(k & 0xff)
+                a.record(stream)
+                fn()
+                b.record(stream)
+            torch.cuda.synchronize()
+            t = sorted(a.elapsed_time(b) for a, b in ev)
+            return {"median_ms": t[K // 2], "min_ms": t[0]}
+
+        clocks = ClockSampler(0)
+        clocks.start()
+        t_precise = timed(precise)
+        t_pred = timed(predicted)
+        t_pad = timed(predicted_padded)
+        t_num = timed(numeric_only)
+        clk = clocks.stop()
+        info = sp.read_numeric_result(nres)
+        predicted()
+        torch.cuda.synchronize()
+        info_c = sp.read_numeric_result(nres)
+        # algorithmic bytes of the numeric pass: A (= B) read once (rpt, col,
+        # val), C written once (col, val) plus nnz_row
+        bytes_num = 4 * (M + 1) + 8 * A.nnz + 8 * Z + 4 * M
+        ach = bytes_num / (t_num["median_ms"] * 1e-3) / 1e9
+        out.append({"workload": name, "nnz_A": A.nnz, "F": F, "Z": Z, "alloc_predicted": alloc,
+                    "alloc_over_Z": alloc / Z if Z else None, "flop_over_Z": F / Z if Z else None,
+                    "overflow_rows": info["overflow_rows"], "overflow_nnz": info["overflow_nnz"],
+                    "status": info_c["status"],
+                    "precise_symbolic_plus_numeric": t_precise,
+                    "predicted_alloc_numeric_compact": t_pred,
+                    "speedup_median": t_precise["median_ms"] / t_pred["median_ms"],
+                    "predicted_alloc_numeric_padded": t_pad,
+                    "speedup_padded_median": t_precise["median_ms"] / t_pad["median_ms"],
+                    "padded_is_exact_product": info["overflow_rows"] == 0,
+                    "numeric_pass": {**t_num, "products_per_s": F / (t_num["median_ms"] * 1e-3),
+                                     "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                                  "frac": ach / peak, "algorithmic_bytes": bytes_num,
+                                                  "peak_source": peak_src}},
+                    "clocks": clk})
+        del c_col, c_val, o_col, o_val
+        torch.cuda.empty_cache()
+    line = {"suite": "numeric", "metric": "ms per numeric SpGEMM: predicted allocation vs exact symbolic phase",
+            "l2": "flushed before every step (512 MiB write)", "steps": K, "results": out}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -568,7 +691,7 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--suite", choices=("predict", "serve", "batch", "accuracy"), default="predict",
+    ap.add_argument("--suite", choices=("predict", "serve", "batch", "accuracy", "numeric"), default="predict",
                     help="predict (default): the headline line; serve / batch: the serving loop "
                          "and the batched predictor")
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -584,6 +707,8 @@ def main(argv=None):
         return run_batch(args)
     if args.suite == "accuracy":
         return run_accuracy(args)
+    if args.suite == "numeric":
+        return run_numeric(args)
     return run_ours(args)
 
 

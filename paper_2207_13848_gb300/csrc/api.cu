@@ -645,9 +645,11 @@ NumArgs numeric_args(const spgemm_csr_t* A, const float* a_val, const spgemm_csr
   return a;
 }
 
-// Warp-per-row pass, block-per-row pass over the rows it queued, finish.
+// Warp-per-row pass, block-per-row pass over the rows it queued, finish;
+// the compaction first moves the rows that fitted.
 int launch_numeric(const DeviceLimits* L, const NumArgs& a, cudaStream_t st) {
   if (a.M > 0) {
+    if (a.mode == kNumCompact) k_numeric_move<<<L->sms * 8, kMoveThreads, 0, st>>>(a);
     const int g = grid_for(a.M, kNumWarps, (long long)L->sms * L->num_blocks_per_sm);
     k_numeric_rows<<<g, kNumThreads, kNumRowsSmem, st>>>(a);
     k_numeric_heavy<<<L->sms, kNumHeavyThreads, kNumHeavySmem, st>>>(a);

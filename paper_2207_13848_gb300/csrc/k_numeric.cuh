@@ -4,7 +4,8 @@
 // sampled compression ratio is for (Sec. I: it replaces the symbolic phase of a
 // two-phase SpGEMM).  A row whose exact size exceeds its predicted share is
 // counted as an overflow; the compaction pass then builds the exact CSR, moving
-// every row that fitted and recomputing the rows that did not.
+// every row that fitted (a flat, balanced copy over the exact layout) and
+// recomputing the rows that did not.
 //
 // Rows are computed row-wise (Gustavson): every product a_ik * b_kc of row i is
 // added into an accumulator keyed by its column c.  Accumulators:
@@ -24,9 +25,9 @@
 
 namespace spg {
 
-constexpr int kNumThreads = 128;                   // warp-per-row pass: 4 warps per block
+constexpr int kNumThreads = 256;                   // warp-per-row pass: 8 warps per block
 constexpr int kNumWarps = kNumThreads / 32;
-constexpr int kNumWarpSlots = 2048;                // (column, value) slots per warp: 16 KB
+constexpr int kNumWarpSlots = 1024;                // (column, value) slots per warp: 8 KB
 constexpr int kNumWarpCap = kNumWarpSlots / 2;     // products per row for the warp path
 constexpr int kNumHeavyThreads = 1024;             // block-per-row pass
 constexpr int kNumBlockSlots = 16384;              // block table: 64 KB of columns + 64 KB of values
@@ -401,19 +402,6 @@ __device__ void num_publish(const NumArgs& a, const NumTally& tl, bool bad) {
   }
 }
 
-// Copies row `row` (it fitted its allocation) into the exact layout.
-__device__ __forceinline__ void num_copy_row_warp(const NumArgs& a, int row, int n) {
-  const int lane = threadIdx.x & 31;
-  const long long src = a.alloc[row], dst = a.out_rpt[row];
-  for (int k = lane; k < n; k += 32) {
-    const long long q = dst + k, sq = src + k;
-    if (q < a.out_cap && sq < a.alloc_cap) {
-      a.out_col[q] = a.c_col[sq];
-      a.out_val[q] = a.c_val[sq];
-    }
-  }
-}
-
 // Warp-per-row pass over all rows (grid-stride over warps).
 __global__ void __launch_bounds__(kNumThreads) k_numeric_rows(NumArgs a) {
   extern __shared__ __align__(16) unsigned char num_dyn[];
@@ -423,21 +411,103 @@ __global__ void __launch_bounds__(kNumThreads) k_numeric_rows(NumArgs a) {
   const long long gw = (long long)blockIdx.x * kNumWarps + warp, nw = (long long)gridDim.x * kNumWarps;
   NumTally tl;
   bool bad = false;
-  for (long long r = gw; r < a.M; r += nw) {
-    const int row = (int)r;
-    if (a.mode == kNumCompact) {
-      const int n = a.nnz_row[row];
-      if (lane == 0 && a.out_rpt[row] + n > a.out_cap) bad = true;  // exact arrays too short
-      if (n <= num_alloc_room(a, row)) {  // it fitted: move it
-        num_copy_row_warp(a, row, n);
-        continue;
+  if (a.mode == kNumCompact) {
+    // only the rows that overflowed their allocation are computed again (the
+    // others are moved by k_numeric_move): 32 rows checked at a time
+    for (long long r0 = gw * 32; r0 < a.M; r0 += nw * 32) {
+      const long long r = r0 + lane;
+      bool over = false;
+      if (r < a.M) {
+        const int n = a.nnz_row[r];
+        if (a.out_rpt[r] + n > a.out_cap) bad = true;  // exact arrays too short
+        over = n > num_alloc_room(a, (int)r);
+      }
+      unsigned m = __ballot_sync(kFull, over);
+      while (m) {
+        const int l = __ffs(m) - 1;
+        m &= m - 1;
+        num_row_warp(a, (int)(r0 + l), keys, vals, bad);
       }
     }
-    const long long nnz = num_row_warp(a, row, keys, vals, bad);
-    if (nnz >= 0 && lane == 0) tl.add(a, row, nnz);
+  } else {
+    for (long long r = gw; r < a.M; r += nw) {
+      const long long nnz = num_row_warp(a, (int)r, keys, vals, bad);
+      if (nnz >= 0 && lane == 0) tl.add(a, (int)r, nnz);
+    }
   }
   bad = __any_sync(kFull, bad);
   if (lane == 0) num_publish(a, tl, bad);
+}
+
+// Compaction, the rows that fitted: the exact layout's positions
+// [0, out_rpt[M]) are split evenly among the warps; warp w finds the row of
+// its first position (a 32-way search over out_rpt), then lane l takes
+// positions q0 + l, q0 + l + 32, ..., following the row boundaries with a
+// cursor, and copies entry q - out_rpt[row] of the row from its allocation.
+// Positions of rows that overflowed are left to the recomputation.
+constexpr int kMoveThreads = 256;
+constexpr int kMoveUnroll = 8;
+__global__ void __launch_bounds__(kMoveThreads) k_numeric_move(NumArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long nw = ((long long)gridDim.x * kMoveThreads) >> 5;
+  const long long w = ((long long)blockIdx.x * kMoveThreads + threadIdx.x) >> 5;
+  const long long Z = a.out_rpt[a.M];
+  const long long q0 = Z * w / nw, q1 = Z * (w + 1) / nw;
+  if (q0 >= q1) return;
+  // the last row r with out_rpt[r] <= q0 (rows with no entries are skipped by the cursor)
+  long long lo = 0, hi = a.M;  // out_rpt[lo] <= q0 < out_rpt[hi] (q0 < Z)
+  while (hi - lo > 1) {
+    const long long step = (hi - lo + 31) / 32;
+    const long long x = lo + (long long)(lane + 1) * step;
+    const bool le = x < hi && a.out_rpt[x] <= q0;
+    const unsigned b = __ballot_sync(kFull, le);
+    const long long nlo = lo + (long long)__popc(b) * step;
+    hi = min(hi, nlo + step);
+    lo = nlo;
+  }
+  // the cursor row: its exact range [rs, re), whether it fitted its
+  // allocation, and the shift from an exact position to its allocation
+  long long row = lo;
+  long long rs = a.out_rpt[row], re = a.out_rpt[row + 1];
+  bool fits = false;
+  long long shift = 0;
+  auto locate = [&]() {
+    fits = re - rs <= num_alloc_room(a, (int)row);
+    shift = a.alloc[row] - rs;
+  };
+  locate();
+  for (long long qb = q0; qb < q1; qb += 32 * kMoveUnroll) {
+    int cv[kMoveUnroll];
+    float vv[kMoveUnroll];
+    long long dq[kMoveUnroll];
+#pragma unroll
+    for (int u = 0; u < kMoveUnroll; ++u) {
+      const long long q = qb + lane + 32 * u;
+      dq[u] = -1;
+      if (q < q1) {
+        if (q >= re) {  // advance to the row holding q
+          do {
+            ++row;
+            rs = re;
+            re = a.out_rpt[row + 1];
+          } while (q >= re);
+          locate();
+        }
+        if (fits) {
+          cv[u] = a.c_col[q + shift];
+          vv[u] = a.c_val[q + shift];
+          dq[u] = q;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kMoveUnroll; ++u) {
+      if (dq[u] >= 0 && dq[u] < a.out_cap) {
+        a.out_col[dq[u]] = cv[u];
+        a.out_val[dq[u]] = vv[u];
+      }
+    }
+  }
 }
 
 // Block-per-row pass over the queued rows.
