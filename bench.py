@@ -597,6 +597,7 @@ def run_numeric(args):
         alloc = presult["pred_total"]
         F = presult["flop_total"]
         nnz_row = torch.empty(M, dtype=torch.int32, device=dev)
+        row_start = torch.empty(M, dtype=torch.int64, device=dev)
         nres = sp.new_numeric_result(dev)
         c_col = torch.empty(max(alloc, Z, 1), dtype=torch.int32, device=dev)
         c_val = torch.empty(max(alloc, Z, 1), dtype=torch.float32, device=dev)
@@ -606,29 +607,27 @@ def run_numeric(args):
         pad_col, pad_val = c_col[:alloc], c_val[:alloc]
         exa_col, exa_val = c_col[:Z], c_val[:Z]
 
+        def ok(*rcs):
+            if any(rcs):
+                raise RuntimeError("numeric call failed: " + ", ".join(sp.spgemm_status_string(r) for r in rcs if r))
+
         def precise():
-            r1 = sp.spgemm_symbolic_exact(dA, dA, ex.pred, ex.offsets, ex.res, ws, stream)
-            r2 = sp.spgemm_numeric_into(dA, val, dA, val, ex.offsets, exa_col, exa_val, nnz_row, nres, ws, stream)
-            if r1 or r2:
-                raise RuntimeError("precise method failed")
+            ok(sp.spgemm_symbolic_exact(dA, dA, ex.pred, ex.offsets, ex.res, ws, stream),
+               sp.spgemm_numeric_into(dA, val, dA, val, ex.offsets, exa_col, exa_val, row_start, nnz_row, nres,
+                                      ws, stream))
 
-        def predicted():
-            r1 = sp.spgemm_predict_structure(dA, dA, cfg, pr.pred, pr.offsets, None, pr.res, ws, stream)
-            r2 = sp.spgemm_numeric_into(dA, val, dA, val, pr.offsets, pad_col, pad_val, nnz_row, nres, ws, stream)
-            r3 = sp.spgemm_numeric_compact(dA, val, dA, val, pr.offsets, pad_col, pad_val, nnz_row, o_rpt, o_col,
-                                           o_val, nres, ws, stream)
-            if r1 or r2 or r3:
-                raise RuntimeError("predicted allocation failed")
+        def into(pool):
+            ok(sp.spgemm_predict_structure(dA, dA, cfg, pr.pred, pr.offsets, None, pr.res, ws, stream),
+               sp.spgemm_numeric_into(dA, val, dA, val, None if pool else pr.offsets, pad_col, pad_val, row_start,
+                                      nnz_row, nres, ws, stream))
 
-        def predicted_padded():
-            r1 = sp.spgemm_predict_structure(dA, dA, cfg, pr.pred, pr.offsets, None, pr.res, ws, stream)
-            r2 = sp.spgemm_numeric_into(dA, val, dA, val, pr.offsets, pad_col, pad_val, nnz_row, nres, ws, stream)
-            if r1 or r2:
-                raise RuntimeError("predicted allocation failed")
+        def into_compact(pool):
+            into(pool)
+            ok(sp.spgemm_numeric_compact(dA, val, dA, val, pad_col, pad_val, row_start, nnz_row, o_rpt, o_col,
+                                         o_val, nres, ws, stream))
 
         def numeric_only():
-            if sp.spgemm_numeric_into(dA, val, dA, val, pr.offsets, pad_col, pad_val, nnz_row, nres, ws, stream):
-                raise RuntimeError("numeric pass failed")
+            ok(sp.spgemm_numeric_into(dA, val, dA, val, None, pad_col, pad_val, row_start, nnz_row, nres, ws, stream))
 
         def timed(fn):
             for _ in range(3):
@@ -647,28 +646,29 @@ def run_numeric(args):
         clocks = ClockSampler(0)
         clocks.start()
         t_precise = timed(precise)
-        t_pred = timed(predicted)
-        t_pad = timed(predicted_padded)
+        modes = {}
+        for mode, pool in (("per_row_shares", False), ("pool_of_predicted_total", True)):
+            t_c = timed(lambda: into_compact(pool))
+            t_i = timed(lambda: into(pool))
+            into(pool)
+            torch.cuda.synchronize()
+            inf = sp.read_numeric_result(nres)
+            into_compact(pool)
+            torch.cuda.synchronize()
+            modes[mode] = {"overflow_rows": inf["overflow_rows"], "overflow_nnz": inf["overflow_nnz"],
+                           "exact_csr_ms": t_c, "speedup_exact_csr": t_precise["median_ms"] / t_c["median_ms"],
+                           "row_layout_ms": t_i, "row_layout_complete": inf["overflow_rows"] == 0,
+                           "speedup_row_layout": t_precise["median_ms"] / t_i["median_ms"],
+                           "status": sp.read_numeric_result(nres)["status"]}
         t_num = timed(numeric_only)
         clk = clocks.stop()
-        info = sp.read_numeric_result(nres)
-        predicted()
-        torch.cuda.synchronize()
-        info_c = sp.read_numeric_result(nres)
         # algorithmic bytes of the numeric pass: A (= B) read once (rpt, col,
         # val), C written once (col, val) plus nnz_row
         bytes_num = 4 * (M + 1) + 8 * A.nnz + 8 * Z + 4 * M
         ach = bytes_num / (t_num["median_ms"] * 1e-3) / 1e9
         out.append({"workload": name, "nnz_A": A.nnz, "F": F, "Z": Z, "alloc_predicted": alloc,
                     "alloc_over_Z": alloc / Z if Z else None, "flop_over_Z": F / Z if Z else None,
-                    "overflow_rows": info["overflow_rows"], "overflow_nnz": info["overflow_nnz"],
-                    "status": info_c["status"],
-                    "precise_symbolic_plus_numeric": t_precise,
-                    "predicted_alloc_numeric_compact": t_pred,
-                    "speedup_median": t_precise["median_ms"] / t_pred["median_ms"],
-                    "predicted_alloc_numeric_padded": t_pad,
-                    "speedup_padded_median": t_precise["median_ms"] / t_pad["median_ms"],
-                    "padded_is_exact_product": info["overflow_rows"] == 0,
+                    "precise_symbolic_plus_numeric": t_precise, "predicted": modes,
                     "numeric_pass": {**t_num, "products_per_s": F / (t_num["median_ms"] * 1e-3),
                                      "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                                   "frac": ach / peak, "algorithmic_bytes": bytes_num,

@@ -316,16 +316,24 @@ int spgemm_batch_autotune(const spgemm_batch_item_t* items, int32_t n, void* ws,
 /* ---- the consumer: numeric product into the predicted allocation -----------------------
  * The prediction exists to size C before the numeric phase of C = A*B (Sec. I:
  * it replaces the symbolic phase of a two-phase SpGEMM).  These two calls are
- * that numeric phase.  spgemm_numeric_into computes every row of C into the
- * row layout alloc_offsets (normally the offsets of spgemm_predict_structure),
- * writes each row's exact nnz, and counts the rows that did not fit their
- * share.  spgemm_numeric_compact then builds the exact CSR of C: rows that
- * fitted are moved, rows that overflowed are computed again straight into their
- * exact place.  A caller that can use the padded layout as is (no overflow, or
- * its own handling) may skip the compaction.
+ * that numeric phase.  spgemm_numeric_into computes every row of C into an
+ * allocation sized by the prediction, in one of two ways:
+ *   - per-row shares (alloc_offsets given, normally the offsets of
+ *     spgemm_predict_structure): row i goes to c_col/c_val[alloc_offsets[i] ..]
+ *     when its exact nnz is at most alloc_offsets[i+1] - alloc_offsets[i];
+ *   - one pool (alloc_offsets NULL) of c_capacity entries, normally the
+ *     predicted total pred_total = offsets[M] (Z2*, Eq. 4) plus any slack:
+ *     each row takes exactly its nnz from the pool, at a position of the
+ *     library's choosing, while the pool has room.
+ * It writes each row's exact nnz (nnz_row) and start (row_start; -1 when the
+ * row did not fit: an overflow, counted in res).  spgemm_numeric_compact then
+ * builds the exact CSR of C: rows that were written are moved, rows that
+ * overflowed are computed again straight into their exact place.  A caller
+ * that can use (row_start, nnz_row) as is may skip the compaction when no row
+ * overflowed.
  *
  * Values are single precision: a_val[nnz(A)], b_val[nnz(B)] in CSR order;
- * c_val[i] = sum_k a_ik * b_kc, summed in single precision in no fixed order
+ * c_val = sum_k a_ik * b_kc, summed in single precision in no fixed order
  * (the structure is exact; a value differs from the exact sum by at most
  * (terms + 1) * 2^-24 * sum_k |a_ik * b_kc|).  Column ids within a row come
  * out in no particular order.  Structural entries are kept even when their sum
@@ -334,34 +342,32 @@ int spgemm_batch_autotune(const spgemm_batch_item_t* items, int32_t n, void* ws,
 /* Scalars of a numeric call (device memory, caller-owned). */
 typedef struct spgemm_numeric_result {
   int64_t nnz_total;     /* NNZ(C) (spgemm_numeric_into) */
-  int64_t overflow_rows; /* rows whose exact nnz exceeded their share of the allocation */
+  int64_t overflow_rows; /* rows that did not fit the allocation */
   int64_t overflow_nnz;  /* the nnz of those rows */
-  int64_t alloc_total;   /* alloc_offsets[A.rows] */
+  int64_t alloc_total;   /* alloc_offsets[A.rows] (shares) or c_capacity (pool) */
   int32_t status;        /* SPGEMM_STATUS_* bits (ERR_BAD_INPUT: an id or offset out of range) */
   int32_t reserved;
 } spgemm_numeric_result_t;
 
-/* Row i of C goes to c_col/c_val[alloc_offsets[i] ..] when its exact nnz is at
- * most alloc_offsets[i+1] - alloc_offsets[i]; otherwise nothing of it is kept
- * there (the row counts as an overflow).  nnz_row[i] receives the exact nnz of
- * every row (int32[A.rows]).  alloc_offsets (int64[A.rows + 1]) must be
- * non-decreasing; c_col (int32) and c_val (float) hold c_capacity entries, and
- * nothing is written at or past c_capacity.  res is overwritten.  The workspace
- * is the one of spgemm_workspace_size(A, B). */
+/* alloc_offsets (int64[A.rows + 1], non-decreasing) or NULL for the pool mode;
+ * c_col (int32) and c_val (float) hold c_capacity entries, and nothing is
+ * written at or past c_capacity.  row_start (int64[A.rows]) and nnz_row
+ * (int32[A.rows]) are outputs.  res is overwritten.  The workspace is the one
+ * of spgemm_workspace_size(A, B). */
 int spgemm_numeric_into(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t* B,
                         const float* b_val, const int64_t* alloc_offsets, int32_t* c_col,
-                        float* c_val, int64_t c_capacity, int32_t* nnz_row,
+                        float* c_val, int64_t c_capacity, int64_t* row_start, int32_t* nnz_row,
                         spgemm_numeric_result_t* res, void* ws, size_t ws_bytes, void* stream);
 
 /* The exact CSR of C from the output of spgemm_numeric_into (same A, B, values,
- * alloc_offsets, c_col, c_val, nnz_row): out_rpt = exclusive scan of nnz_row
- * (int64[A.rows + 1], out_rpt[A.rows] = NNZ(C)); out_col/out_val hold
+ * c_col, c_val, c_capacity, row_start, nnz_row): out_rpt = exclusive scan of
+ * nnz_row (int64[A.rows + 1], out_rpt[A.rows] = NNZ(C)); out_col/out_val hold
  * out_capacity >= NNZ(C) entries (res->nnz_total after spgemm_numeric_into).
  * res->status gains the bits of this call; its other fields are kept. */
 int spgemm_numeric_compact(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t* B,
-                           const float* b_val, const int64_t* alloc_offsets, const int32_t* c_col,
-                           const float* c_val, int64_t c_capacity, const int32_t* nnz_row,
-                           int64_t* out_rpt, int32_t* out_col, float* out_val, int64_t out_capacity,
+                           const float* b_val, const int32_t* c_col, const float* c_val, int64_t c_capacity,
+                           const int64_t* row_start, const int32_t* nnz_row, int64_t* out_rpt,
+                           int32_t* out_col, float* out_val, int64_t out_capacity,
                            spgemm_numeric_result_t* res, void* ws, size_t ws_bytes, void* stream);
 
 /* Static description of a host return code or of a status bit set. */

@@ -134,8 +134,8 @@ def load():
     lib.spgemm_status_string.restype = ctypes.c_char_p
     lib.spgemm_status_string.argtypes = [ctypes.c_int]
     i64 = ctypes.c_int64
-    lib.spgemm_numeric_into.argtypes = [C, P, C, P, P, P, P, i64, P, P, P, sz, P]
-    lib.spgemm_numeric_compact.argtypes = [C, P, C, P, P, P, P, i64, P, P, P, P, i64, P, P, sz, P]
+    lib.spgemm_numeric_into.argtypes = [C, P, C, P, P, P, P, i64, P, P, P, P, sz, P]
+    lib.spgemm_numeric_compact.argtypes = [C, P, C, P, P, P, i64, P, P, P, P, P, i64, P, P, sz, P]
     lib.spgemm_numeric_into.restype = ctypes.c_int
     lib.spgemm_numeric_compact.restype = ctypes.c_int
     for fn in (lib.spgemm_flop_per_row, lib.spgemm_predict_cr, lib.spgemm_predict_structure,
@@ -320,23 +320,23 @@ def _numel(t):
     return 0 if t is None else int(t.numel())
 
 
-def spgemm_numeric_into(A, a_val, B, b_val, alloc_offsets, c_col, c_val, nnz_row, res, ws, stream=None):
-    """C = A*B into the allocation layout alloc_offsets (see include/spgemm_predict.h)."""
+def spgemm_numeric_into(A, a_val, B, b_val, alloc_offsets, c_col, c_val, row_start, nnz_row, res, ws, stream=None):
+    """C = A*B into per-row shares (alloc_offsets) or one pool (alloc_offsets None)."""
     a, b = A.struct(), B.struct()
     cap = min(_numel(c_col), _numel(c_val))
     return load().spgemm_numeric_into(ctypes.byref(a), _ptr(a_val), ctypes.byref(b), _ptr(b_val),
-                                      _ptr(alloc_offsets), _ptr(c_col), _ptr(c_val), cap, _ptr(nnz_row),
-                                      _ptr(res), ws.ptr(), ws.nbytes, _stream(stream))
+                                      _ptr(alloc_offsets), _ptr(c_col), _ptr(c_val), cap, _ptr(row_start),
+                                      _ptr(nnz_row), _ptr(res), ws.ptr(), ws.nbytes, _stream(stream))
 
 
-def spgemm_numeric_compact(A, a_val, B, b_val, alloc_offsets, c_col, c_val, nnz_row, out_rpt, out_col,
-                           out_val, res, ws, stream=None):
+def spgemm_numeric_compact(A, a_val, B, b_val, c_col, c_val, row_start, nnz_row, out_rpt, out_col, out_val, res,
+                           ws, stream=None):
     """The exact CSR of C from spgemm_numeric_into's output."""
     a, b = A.struct(), B.struct()
     cap = min(_numel(c_col), _numel(c_val))
     out_cap = min(_numel(out_col), _numel(out_val))
     return load().spgemm_numeric_compact(ctypes.byref(a), _ptr(a_val), ctypes.byref(b), _ptr(b_val),
-                                         _ptr(alloc_offsets), _ptr(c_col), _ptr(c_val), cap, _ptr(nnz_row),
+                                         _ptr(c_col), _ptr(c_val), cap, _ptr(row_start), _ptr(nnz_row),
                                          _ptr(out_rpt), _ptr(out_col), _ptr(out_val), out_cap, _ptr(res),
                                          ws.ptr(), ws.nbytes, _stream(stream))
 
@@ -529,39 +529,44 @@ class Batch:
 # ---- the consumer: numeric product allocated by the prediction ------------------
 @dataclass
 class NumericProduct:
-    rpt: "object"      # int64[M + 1] exact offsets (device)
+    rpt: "object"      # int64[M + 1] exact offsets (device), or (row_start, nnz_row) without compaction
     col: "object"      # int32[NNZ(C)] (device; column order within a row is free)
     val: "object"      # float32[NNZ(C)] (device)
     info: dict         # prediction and numeric result records, allocation sizes
 
 
-def numeric_product(A, a_val, B, b_val, cfg, ws=None, stream=None, compact=True):
+def numeric_product(A, a_val, B, b_val, cfg, ws=None, stream=None, compact=True, pool=True, slack=0.0):
     """C = A*B the way the prediction is meant to be used: predict the structure,
-    allocate C by the predicted offsets, compute every row into that allocation,
-    then build the exact CSR (rows that fitted are moved, rows that overflowed are
-    computed again).  One host read of the numeric result sizes the exact arrays.
-    With compact=False, returns the padded layout (rpt = the predicted offsets,
-    valid only when no row overflowed) without the compaction."""
+    allocate C by the prediction, compute every row into that allocation, then
+    build the exact CSR (rows that were written are moved, rows that overflowed
+    are computed again).  pool=True allocates the predicted total (times 1 +
+    slack) as one pool; pool=False gives each row its predicted share.  One host
+    read of the numeric result sizes the exact arrays.  With compact=False,
+    returns (row_start, nnz_row) as the row layout, without the compaction (a
+    complete product only when no row overflowed)."""
+    import math
     torch = _torch()
     dev = A.rpt.device
     ws = ws or Workspace.for_operands(A, B)
     pred = predict_structure(A, B, cfg, ws=ws, stream=stream)
     presult = read_result(pred.res)
-    alloc = max(presult["pred_total"], 0)
-    c_col = torch.empty(max(alloc, 1), dtype=torch.int32, device=dev)[:alloc]
-    c_val = torch.empty(max(alloc, 1), dtype=torch.float32, device=dev)[:alloc]
+    total = max(presult["pred_total"], 0)
+    cap = int(math.ceil(total * (1.0 + slack))) if pool else total
+    c_col = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)[:cap]
+    c_val = torch.empty(max(cap, 1), dtype=torch.float32, device=dev)[:cap]
+    row_start = torch.empty(max(A.rows, 0), dtype=torch.int64, device=dev)
     nnz_row = torch.empty(max(A.rows, 0), dtype=torch.int32, device=dev)
     nres = new_numeric_result(dev)
-    _check(spgemm_numeric_into(A, a_val, B, b_val, pred.offsets, c_col, c_val, nnz_row, nres, ws, stream),
-           "spgemm_numeric_into")
-    info = {"prediction": presult, "numeric": read_numeric_result(nres)}
+    _check(spgemm_numeric_into(A, a_val, B, b_val, None if pool else pred.offsets, c_col, c_val, row_start, nnz_row,
+                               nres, ws, stream), "spgemm_numeric_into")
+    info = {"prediction": presult, "numeric": read_numeric_result(nres), "pool": pool}
     if not compact:
-        return NumericProduct(pred.offsets, c_col, c_val, info)
+        return NumericProduct((row_start, nnz_row), c_col, c_val, info)
     Z = info["numeric"]["nnz_total"]
     out_rpt = torch.empty(A.rows + 1, dtype=torch.int64, device=dev)
     out_col = torch.empty(max(Z, 1), dtype=torch.int32, device=dev)[:Z]
     out_val = torch.empty(max(Z, 1), dtype=torch.float32, device=dev)[:Z]
-    _check(spgemm_numeric_compact(A, a_val, B, b_val, pred.offsets, c_col, c_val, nnz_row, out_rpt, out_col,
-                                  out_val, nres, ws, stream), "spgemm_numeric_compact")
+    _check(spgemm_numeric_compact(A, a_val, B, b_val, c_col, c_val, row_start, nnz_row, out_rpt, out_col, out_val,
+                                  nres, ws, stream), "spgemm_numeric_compact")
     info["numeric"]["status"] = read_numeric_result(nres)["status"]
     return NumericProduct(out_rpt, out_col, out_val, info)

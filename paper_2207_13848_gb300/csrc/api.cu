@@ -600,10 +600,11 @@ int batch_prepare(const spgemm_batch_item_t* items, int n, const spgemm_batch_tu
 // ---- numeric product into a given allocation (the consumer of the prediction)
 
 int numeric_check(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t* B, const float* b_val,
-                  const int64_t* alloc, const void* c_col, const void* c_val, int64_t c_capacity,
+                  const void* c_col, const void* c_val, int64_t c_capacity, const int64_t* row_start,
                   const int32_t* nnz_row, const spgemm_numeric_result_t* res, void* ws, size_t ws_bytes) {
-  if (!csr_ok(A) || !csr_ok(B) || !res || !ws || !alloc) return SPGEMM_ERR_INVALID_ARG;
-  if ((A->nnz > 0 && !a_val) || (B->nnz > 0 && !b_val) || (A->rows > 0 && !nnz_row)) return SPGEMM_ERR_INVALID_ARG;
+  if (!csr_ok(A) || !csr_ok(B) || !res || !ws) return SPGEMM_ERR_INVALID_ARG;
+  if ((A->nnz > 0 && !a_val) || (B->nnz > 0 && !b_val)) return SPGEMM_ERR_INVALID_ARG;
+  if (A->rows > 0 && (!nnz_row || !row_start)) return SPGEMM_ERR_INVALID_ARG;
   if (c_capacity < 0 || (c_capacity > 0 && (!c_col || !c_val))) return SPGEMM_ERR_INVALID_ARG;
   if (A->cols != B->rows) return SPGEMM_ERR_DIM_MISMATCH;
   if (!csr_fits(A) || !csr_fits(B)) return SPGEMM_ERR_TOO_LARGE;
@@ -613,8 +614,8 @@ int numeric_check(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t*
 }
 
 NumArgs numeric_args(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t* B, const float* b_val,
-                     const int64_t* alloc, int32_t* c_col, float* c_val, int64_t c_capacity, int32_t* nnz_row,
-                     spgemm_numeric_result_t* res, const Workspace& w) {
+                     const int64_t* alloc, int32_t* c_col, float* c_val, int64_t c_capacity,
+                     int64_t* row_start, int32_t* nnz_row, spgemm_numeric_result_t* res, const Workspace& w) {
   NumArgs a;
   a.M = A->rows;
   a.K = B->rows;
@@ -631,6 +632,10 @@ NumArgs numeric_args(const spgemm_csr_t* A, const float* a_val, const spgemm_csr
   a.c_col = c_col;
   a.c_val = c_val;
   a.alloc_cap = c_capacity;
+  // pool mode: about one stripe per 64 K entries, at most kPoolStripes
+  a.pool_stripes = (int)std::max<long long>(1, std::min<long long>(kPoolStripes, c_capacity >> 16));
+  a.slots = w.slots;
+  a.row_start = reinterpret_cast<long long*>(row_start);
   a.nnz_row = nnz_row;
   a.out_rpt = nullptr;
   a.out_col = nullptr;
@@ -733,34 +738,35 @@ int spgemm_symbolic_exact(const spgemm_csr_t* A, const spgemm_csr_t* B, int32_t*
 
 int spgemm_numeric_into(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t* B,
                         const float* b_val, const int64_t* alloc_offsets, int32_t* c_col,
-                        float* c_val, int64_t c_capacity, int32_t* nnz_row,
+                        float* c_val, int64_t c_capacity, int64_t* row_start, int32_t* nnz_row,
                         spgemm_numeric_result_t* res, void* ws, size_t ws_bytes, void* stream) {
-  int rc = numeric_check(A, a_val, B, b_val, alloc_offsets, c_col, c_val, c_capacity, nnz_row, res, ws, ws_bytes);
+  int rc = numeric_check(A, a_val, B, b_val, c_col, c_val, c_capacity, row_start, nnz_row, res, ws, ws_bytes);
   if (rc) return rc;
   const DeviceLimits* L = limits();
   if (!L) return SPGEMM_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Workspace w = ws_carve(ws, A->rows);
   if (cudaMemsetAsync(res, 0, sizeof(*res), st) != cudaSuccess) return SPGEMM_ERR_CUDA;
-  const NumArgs a = numeric_args(A, a_val, B, b_val, alloc_offsets, c_col, c_val, c_capacity, nnz_row, res, w);
+  const NumArgs a = numeric_args(A, a_val, B, b_val, alloc_offsets, c_col, c_val, c_capacity, row_start, nnz_row,
+                                 res, w);
   return launch_numeric(L, a, st);
 }
 
 int spgemm_numeric_compact(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t* B,
-                           const float* b_val, const int64_t* alloc_offsets, const int32_t* c_col,
-                           const float* c_val, int64_t c_capacity, const int32_t* nnz_row,
-                           int64_t* out_rpt, int32_t* out_col, float* out_val, int64_t out_capacity,
-                           spgemm_numeric_result_t* res, void* ws, size_t ws_bytes, void* stream) {
-  int rc = numeric_check(A, a_val, B, b_val, alloc_offsets, c_col, c_val, c_capacity, nnz_row, res, ws, ws_bytes);
+                           const float* b_val, const int32_t* c_col, const float* c_val, int64_t c_capacity,
+                           const int64_t* row_start, const int32_t* nnz_row, int64_t* out_rpt, int32_t* out_col,
+                           float* out_val, int64_t out_capacity, spgemm_numeric_result_t* res, void* ws,
+                           size_t ws_bytes, void* stream) {
+  int rc = numeric_check(A, a_val, B, b_val, c_col, c_val, c_capacity, row_start, nnz_row, res, ws, ws_bytes);
   if (rc) return rc;
   if (!out_rpt || out_capacity < 0 || (out_capacity > 0 && (!out_col || !out_val))) return SPGEMM_ERR_INVALID_ARG;
   const DeviceLimits* L = limits();
   if (!L) return SPGEMM_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Workspace w = ws_carve(ws, A->rows);
-  // the rows that fitted are only read here
-  NumArgs a = numeric_args(A, a_val, B, b_val, alloc_offsets, const_cast<int32_t*>(c_col),
-                           const_cast<float*>(c_val), c_capacity, const_cast<int32_t*>(nnz_row), res, w);
+  // the allocation, row_start and nnz_row are only read here
+  NumArgs a = numeric_args(A, a_val, B, b_val, nullptr, const_cast<int32_t*>(c_col), const_cast<float*>(c_val),
+                           c_capacity, const_cast<int64_t*>(row_start), const_cast<int32_t*>(nnz_row), res, w);
   a.mode = kNumCompact;
   a.out_rpt = reinterpret_cast<const long long*>(out_rpt);
   a.out_col = out_col;

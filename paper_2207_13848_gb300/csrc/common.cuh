@@ -52,7 +52,8 @@ struct alignas(64) Slot {
   long long ftot;   // sum of the block's complete-row FLOP
   unsigned long long tot_ep;  // (epoch << 32) | total, or | 0xffffffff when total
                               // needs 32 bits or more (then read `total`)
-  long long pad1[2];
+  unsigned long long pool;    // numeric product, pool mode: entries taken from stripe s (slot s)
+  long long pad1;
 };
 
 struct Workspace {

@@ -1,11 +1,18 @@
-// Numeric product C = A*B written into a given row layout: the consumer of the
-// predicted structure.  The prediction (Eq. 4 per row, scanned into offsets)
-// sizes the allocation of C before any product is formed, which is what the
-// sampled compression ratio is for (Sec. I: it replaces the symbolic phase of a
-// two-phase SpGEMM).  A row whose exact size exceeds its predicted share is
-// counted as an overflow; the compaction pass then builds the exact CSR, moving
-// every row that fitted (a flat, balanced copy over the exact layout) and
-// recomputing the rows that did not.
+// Numeric product C = A*B written into an allocation sized by the prediction:
+// the consumer of the predicted structure.  The prediction sizes the memory of
+// C before any product is formed, which is what the sampled compression ratio
+// is for (Sec. I: it replaces the symbolic phase of a two-phase SpGEMM).  Two
+// ways to use it:
+//   - per-row shares: row i goes to alloc[i] when its exact size fits
+//     alloc[i+1] - alloc[i] (the offsets of Eq. 4 per row);
+//   - one pool of the predicted total (Z2* = F z*/f*, Eq. 4): each row takes
+//     exactly its size from one of kPoolStripes bump pointers over equal slices
+//     of the pool (the stripe chosen by a hash of the row, the next ones when it
+//     is full), so the rows' positions follow their completion, not their order.
+// Either way the start of every row is recorded (-1 when it did not fit, an
+// overflow).  The compaction pass then builds the exact CSR: every row that was
+// written moves (a flat, balanced copy over the exact layout), the rows that
+// overflowed are computed again.
 //
 // Rows are computed row-wise (Gustavson): every product a_ik * b_kc of row i is
 // added into an accumulator keyed by its column c.  Accumulators:
@@ -32,13 +39,15 @@ constexpr int kNumWarpCap = kNumWarpSlots / 2;     // products per row for the w
 constexpr int kNumHeavyThreads = 1024;             // block-per-row pass
 constexpr int kNumBlockSlots = 16384;              // block table: 64 KB of columns + 64 KB of values
 constexpr int kNumBlockCap = kNumBlockSlots / 2;   // products per row for the block table
-constexpr int kNumDenseCols = 16384;               // columns per dense pass (64 KB of values)
-constexpr int kNumDenseWords = kNumDenseCols / 32;  // its occupancy bitmap (2 KB)
+constexpr int kNumDenseCols = 49152;               // columns per dense pass (192 KB of values)
+constexpr int kNumDenseWords = kNumDenseCols / 32;  // its occupancy bitmap (6 KB)
+constexpr int kPoolStripes = 64;                   // pool mode: bump pointers (one per workspace slot)
 
 constexpr size_t kNumRowsSmem = (size_t)kNumWarps * kNumWarpSlots * (sizeof(int) + sizeof(float));
-constexpr size_t kNumHeavySmem = (size_t)kNumBlockSlots * (sizeof(int) + sizeof(float));
-static_assert((size_t)kNumDenseCols * sizeof(float) + kNumDenseWords * sizeof(unsigned) <= kNumHeavySmem,
-              "dense pass fits the block table's space");
+constexpr size_t kNumBlockTableSmem = (size_t)kNumBlockSlots * (sizeof(int) + sizeof(float));
+constexpr size_t kNumDenseSmem = (size_t)kNumDenseCols * sizeof(float) + kNumDenseWords * sizeof(unsigned);
+// the block-per-row pass runs on its own, so it takes shared memory over L1
+constexpr size_t kNumHeavySmem = kNumDenseSmem > kNumBlockTableSmem ? kNumDenseSmem : kNumBlockTableSmem;
 
 enum NumMode { kNumInto = 0, kNumCompact = 1 };
 
@@ -50,10 +59,14 @@ struct NumArgs {
   const int* b_rpt;
   const int* b_col;
   const float* b_val;
-  const long long* alloc;  // [M + 1] allocation layout of C (the predicted offsets)
-  int* c_col;              // entries in the allocation layout (alloc_cap of them)
+  const long long* alloc;  // [M + 1] per-row shares of the allocation, or null: one pool
+  int* c_col;              // the allocation (alloc_cap entries)
   float* c_val;
   long long alloc_cap;
+  int pool_stripes;        // pool mode: stripes of the pool in use (1 .. kPoolStripes)
+  Slot* slots;             // pool mode: slots[s].pool is stripe s's bump pointer
+  long long* row_start;    // [M] where each row was written in the allocation (-1: not written);
+                           // written by kNumInto, read by kNumCompact
   int* nnz_row;            // [M] exact nnz per row: written by kNumInto, read by kNumCompact
   const long long* out_rpt;  // kNumCompact: [M + 1] exact offsets
   int* out_col;              // kNumCompact: the exact CSR's entries (out_cap of them)
@@ -95,16 +108,36 @@ __device__ __forceinline__ int num_slot(int* keys, int lg, int key) {
   return -1;
 }
 
-// Room for row `row` in the allocation: its share alloc[row+1] - alloc[row],
-// cut to what the arrays hold (alloc_cap entries).  A row needing more is an
-// overflow, in the numeric pass and in the compaction alike.
+// Room for row `row` in its share of the allocation: alloc[row+1] - alloc[row],
+// cut to what the arrays hold (alloc_cap entries).
 __device__ __forceinline__ long long num_alloc_room(const NumArgs& a, int row) {
   const long long d = a.alloc[row], cap = a.alloc[row + 1] - d;
   if (d < 0 || cap <= 0 || d >= a.alloc_cap) return 0;
   return min(cap, a.alloc_cap - d);
 }
 
-// Where a row goes: its first entry's index and its capacity in the target.
+// Pool mode: n entries from a stripe of the pool (the row's stripe first);
+// returns their first position, or -1 when no stripe has room.
+__device__ long long num_pool_take(const NumArgs& a, int row, long long n) {
+  if (n == 0) return 0;
+  const int S = a.pool_stripes;
+  const long long size = (a.alloc_cap + S - 1) / S;
+  const int s0 = (int)((((unsigned)row * 2654435761u) >> 16) % (unsigned)S);
+  for (int k = 0; k < S; ++k) {
+    const int st = (s0 + k) % S;
+    const long long base = (long long)st * size, len = min(a.alloc_cap - base, size);
+    if (len < n) continue;
+    unsigned long long* ctr = &a.slots[st].pool;
+    if ((long long)*reinterpret_cast<volatile unsigned long long*>(ctr) + n > len) continue;  // full
+    const long long pos = (long long)atomicAdd(ctr, (unsigned long long)n);
+    if (pos + n <= len) return base + pos;
+  }
+  return -1;
+}
+
+// Where a row of n entries goes: its first entry's index and its capacity in
+// the target (0 when it does not fit).  Called by one thread per row; in the
+// numeric pass it also records the row's start (or -1).
 struct NumTarget {
   long long dst, cap;
   int* col;
@@ -112,14 +145,22 @@ struct NumTarget {
   long long limit;  // the target arrays' length: nothing is written at or past it
 };
 
-__device__ __forceinline__ NumTarget num_target(const NumArgs& a, int row) {
+__device__ NumTarget num_target(const NumArgs& a, int row, long long n) {
   NumTarget t;
   if (a.mode == kNumInto) {
-    t.dst = a.alloc[row];
-    t.cap = num_alloc_room(a, row);
     t.col = a.c_col;
     t.val = a.c_val;
     t.limit = a.alloc_cap;
+    if (a.alloc) {
+      t.dst = a.alloc[row];
+      t.cap = num_alloc_room(a, row);
+    } else {
+      t.dst = num_pool_take(a, row, n);
+      t.cap = t.dst >= 0 ? n : 0;
+    }
+    const bool fits = t.dst >= 0 && n <= t.cap;
+    a.row_start[row] = fits ? t.dst : -1;
+    if (!fits) t.cap = 0;
   } else {
     t.dst = a.out_rpt[row];
     t.cap = a.out_rpt[row + 1] - t.dst;
@@ -127,7 +168,10 @@ __device__ __forceinline__ NumTarget num_target(const NumArgs& a, int row) {
     t.val = a.out_val;
     t.limit = a.out_cap;
   }
-  if (t.cap < 0 || t.dst < 0) t.cap = 0;
+  if (t.cap < 0 || t.dst < 0) {
+    t.cap = 0;
+    t.dst = 0;
+  }
   return t;
 }
 
@@ -223,7 +267,13 @@ __device__ long long num_row_warp(const NumArgs& a, int row, int* keys, float* v
   // count, then write when the row fits its target
   int nnz = 0;
   for (int i0 = 0; i0 < P; i0 += 32) nnz += __popc(__ballot_sync(kFull, keys[i0 + lane] != -1));
-  const NumTarget t = num_target(a, row);
+  NumTarget t;
+  if (lane == 0) t = num_target(a, row, nnz);
+  t.dst = __shfl_sync(kFull, t.dst, 0);
+  t.cap = __shfl_sync(kFull, t.cap, 0);
+  t.limit = __shfl_sync(kFull, t.limit, 0);
+  t.col = a.mode == kNumInto ? a.c_col : a.out_col;
+  t.val = a.mode == kNumInto ? a.c_val : a.out_val;
   if (nnz <= t.cap) {
     int pos = 0;
     for (int i0 = 0; i0 < P; i0 += 32) {
@@ -245,13 +295,14 @@ struct NumHeavySmem {
   long long bs[kNumHeavyThreads];
   float av[kNumHeavyThreads];
   long long red[kNumHeavyThreads / 32 + 1];
-  int flag;
+  long long tgt[3];  // the row's target, from thread 0: dst, cap, limit
 };
 
 // Calls f(col, value) for every product of A's row [rb, re) once, by the whole
 // block (warp w takes a contiguous run of each group's products, lanes
-// interleaved for coalesced reads of B).
-template <class F>
+// interleaved for coalesced reads of B).  Without VAL, B's values are not read
+// (f gets 0).
+template <bool VAL = true, class F>
 __device__ void num_block_products(const NumArgs& a, long long rb, long long re, NumHeavySmem& sm, bool& bad,
                                    F&& f) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -288,7 +339,7 @@ __device__ void num_block_products(const NumArgs& a, long long rb, long long re,
           bad = true;
           continue;
         }
-        f(col, sm.av[o] * __ldg(a.b_val + q));
+        f(col, VAL ? sm.av[o] * __ldg(a.b_val + q) : 0.0f);
       }
     }
     __syncthreads();
@@ -307,7 +358,23 @@ __device__ long long num_row_block(const NumArgs& a, int row, NumHeavySmem& sm, 
     fl += len;
   }
   const long long flop = block_sum<kNumHeavyThreads>(fl, sm.red);
-  const NumTarget tg = num_target(a, row);
+  // the row's target, from thread 0, once its size n is known
+  auto target = [&](long long n) {
+    if (t == 0) {
+      const NumTarget x = num_target(a, row, n);
+      sm.tgt[0] = x.dst;
+      sm.tgt[1] = x.cap;
+      sm.tgt[2] = x.limit;
+    }
+    __syncthreads();
+    NumTarget x;
+    x.dst = sm.tgt[0];
+    x.cap = sm.tgt[1];
+    x.limit = sm.tgt[2];
+    x.col = a.mode == kNumInto ? a.c_col : a.out_col;
+    x.val = a.mode == kNumInto ? a.c_val : a.out_val;
+    return x;
+  };
   if (flop <= kNumBlockCap) {
     int* keys = reinterpret_cast<int*>(dyn);
     float* vals = reinterpret_cast<float*>(dyn + (size_t)kNumBlockSlots * sizeof(int));
@@ -329,60 +396,82 @@ __device__ long long num_row_block(const NumArgs& a, int row, NumHeavySmem& sm, 
     for (int i = s0; i < s1; ++i) c += keys[i] != -1;
     long long nnz;
     long long pos = block_excl_scan<kNumHeavyThreads>(c, sm.red, &nnz);
+    const NumTarget tg = target(nnz);
     if (nnz <= tg.cap)
       for (int i = s0; i < s1; ++i)
         if (keys[i] != -1) num_put(tg, pos++, keys[i], vals[i]);
     __syncthreads();
     return nnz;
   }
-  // dense passes over B's columns, kNumDenseCols at a time; entries are
-  // written while they fit (a row that overflows is recomputed later)
+  // dense passes over B's columns, kNumDenseCols at a time (entries in
+  // ascending column order).  A share or an exact slot is known up front: one
+  // sweep writes and counts.  A place in the pool needs the row's size first:
+  // one sweep counts, the next writes.
   float* acc = reinterpret_cast<float*>(dyn);
   unsigned* bits = reinterpret_cast<unsigned*>(dyn + (size_t)kNumDenseCols * sizeof(float));
-  long long nnz = 0;
-  for (long long lo = 0; lo < a.N; lo += kNumDenseCols) {
-    const long long hi = min(a.N, lo + (long long)kNumDenseCols);
-    for (int i = t; i < kNumDenseCols; i += kNumHeavyThreads) acc[i] = 0.0f;
-    for (int i = t; i < kNumDenseWords; i += kNumHeavyThreads) bits[i] = 0u;
-    __syncthreads();
-    num_block_products(a, rb, re, sm, bad, [&](int col, float v) {
-      if (col >= lo && col < hi) {
-        const int o = (int)(col - lo);
-        atomicAdd(&acc[o], v);
-        atomicOr(&bits[o >> 5], 1u << (o & 31));
+  auto sweep = [&](bool write, const NumTarget& tg) -> long long {
+    long long nnz = 0;
+    for (long long lo = 0; lo < a.N; lo += kNumDenseCols) {
+      const long long hi = min(a.N, lo + (long long)kNumDenseCols);
+      for (int i = t; i < kNumDenseCols; i += kNumHeavyThreads) acc[i] = 0.0f;
+      for (int i = t; i < kNumDenseWords; i += kNumHeavyThreads) bits[i] = 0u;
+      __syncthreads();
+      auto mark = [&](int col, float v) {
+        if (col >= lo && col < hi) {
+          const int o = (int)(col - lo);
+          if (write) atomicAdd(&acc[o], v);
+          atomicOr(&bits[o >> 5], 1u << (o & 31));
+        }
+      };
+      if (write) num_block_products<true>(a, rb, re, sm, bad, mark);
+      else num_block_products<false>(a, rb, re, sm, bad, mark);
+      // thread t owns bitmap words [t * per, (t + 1) * per): ascending columns
+      constexpr int per = (kNumDenseWords + kNumHeavyThreads - 1) / kNumHeavyThreads;
+      const int w0 = min(kNumDenseWords, t * per), w1 = min(kNumDenseWords, w0 + per);
+      long long c = 0;
+      for (int w = w0; w < w1; ++w) c += __popc(bits[w]);
+      long long cnt;
+      long long pos = nnz + block_excl_scan<kNumHeavyThreads>(c, sm.red, &cnt);
+      if (write) {
+        for (int w = w0; w < w1; ++w) {
+          unsigned m = bits[w];
+          while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int o = w * 32 + b;
+            num_put(tg, pos++, (int)(lo + o), acc[o]);
+          }
+        }
       }
-    });
-    // thread t owns bitmap words [t * per, (t + 1) * per): ascending columns
-    constexpr int per = (kNumDenseWords + kNumHeavyThreads - 1) / kNumHeavyThreads;
-    const int w0 = min(kNumDenseWords, t * per), w1 = min(kNumDenseWords, w0 + per);
-    long long c = 0;
-    for (int w = w0; w < w1; ++w) c += __popc(bits[w]);
-    long long cnt;
-    long long pos = nnz + block_excl_scan<kNumHeavyThreads>(c, sm.red, &cnt);
-    for (int w = w0; w < w1; ++w) {
-      unsigned m = bits[w];
-      while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        const int o = w * 32 + b;
-        num_put(tg, pos++, (int)(lo + o), acc[o]);
-      }
+      nnz += cnt;
+      __syncthreads();
     }
-    nnz += cnt;
-    __syncthreads();
+    return nnz;
+  };
+  long long nnz;
+  if (a.mode == kNumCompact) {  // the exact slot is known
+    nnz = sweep(true, target(a.nnz_row[row]));
+  } else if (a.alloc) {  // a share: written while it fits, dropped if the row turns out larger
+    const NumTarget tg = target(0);
+    nnz = sweep(true, tg);
+    if (t == 0 && nnz > tg.cap) a.row_start[row] = -1;
+  } else {  // the pool: the size first, then the entries
+    nnz = sweep(false, NumTarget{});
+    const NumTarget tg = target(nnz);
+    if (tg.cap >= nnz && nnz > 0) sweep(true, tg);
   }
   return nnz;
 }
 
-// Records one computed row: its nnz (kNumInto) and, when it did not fit its
-// allocation, the overflow (per-thread sums, added by the block at the end).
+// Records one computed row: its nnz (kNumInto) and, when it was not written
+// (row_start = -1), the overflow (per-thread sums, added at the end).
 struct NumTally {
   long long nnz = 0, over_rows = 0, over_nnz = 0;
   __device__ void add(const NumArgs& a, int row, long long nnz_row) {
     nnz += nnz_row;
     if (a.mode == kNumInto) {
       a.nnz_row[row] = (int)nnz_row;
-      if (nnz_row > num_alloc_room(a, row)) {
+      if (a.row_start[row] < 0) {
         over_rows += 1;
         over_nnz += nnz_row;
       }
@@ -420,7 +509,7 @@ __global__ void __launch_bounds__(kNumThreads) k_numeric_rows(NumArgs a) {
       if (r < a.M) {
         const int n = a.nnz_row[r];
         if (a.out_rpt[r] + n > a.out_cap) bad = true;  // exact arrays too short
-        over = n > num_alloc_room(a, (int)r);
+        over = a.row_start[r] < 0;
       }
       unsigned m = __ballot_sync(kFull, over);
       while (m) {
@@ -439,11 +528,11 @@ __global__ void __launch_bounds__(kNumThreads) k_numeric_rows(NumArgs a) {
   if (lane == 0) num_publish(a, tl, bad);
 }
 
-// Compaction, the rows that fitted: the exact layout's positions
+// Compaction, the rows that were written: the exact layout's positions
 // [0, out_rpt[M]) are split evenly among the warps; warp w finds the row of
 // its first position (a 32-way search over out_rpt), then lane l takes
 // positions q0 + l, q0 + l + 32, ..., following the row boundaries with a
-// cursor, and copies entry q - out_rpt[row] of the row from its allocation.
+// cursor, and copies entry q - out_rpt[row] of the row from row_start[row].
 // Positions of rows that overflowed are left to the recomputation.
 constexpr int kMoveThreads = 256;
 constexpr int kMoveUnroll = 8;
@@ -472,8 +561,9 @@ __global__ void __launch_bounds__(kMoveThreads) k_numeric_move(NumArgs a) {
   bool fits = false;
   long long shift = 0;
   auto locate = [&]() {
-    fits = re - rs <= num_alloc_room(a, (int)row);
-    shift = a.alloc[row] - rs;
+    const long long st = a.row_start[row];
+    fits = st >= 0 && st + (re - rs) <= a.alloc_cap;
+    shift = st - rs;
   };
   locate();
   for (long long qb = q0; qb < q1; qb += 32 * kMoveUnroll) {
@@ -539,7 +629,8 @@ __global__ void k_numeric_finish(NumArgs a, unsigned* hdr_status) {
   const unsigned n = *hc;
   if ((long long)n > a.heavy_cap) atomicOr(a.status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
   *hc = 0;
-  if (a.mode == kNumInto) a.res->alloc_total = a.M > 0 ? a.alloc[a.M] : 0;
+  if (a.mode == kNumInto) a.res->alloc_total = a.alloc ? (a.M > 0 ? a.alloc[a.M] : 0) : a.alloc_cap;
+  for (int st = 0; st < kPoolStripes; ++st) a.slots[st].pool = 0;
   a.res->status |= (int)*reinterpret_cast<volatile unsigned*>(hdr_status);
   *reinterpret_cast<volatile unsigned*>(hdr_status) = 0u;
 }

@@ -89,7 +89,8 @@ def _check_against_oracle(A, B, av, bv, rpt, col, val, what):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_numeric_product_matches_oracle(name):
+@pytest.mark.parametrize("pool", [False, True])
+def test_numeric_product_matches_oracle(name, pool):
     A, B = CASES[name]
     B = A if B is None else B
     av = _values(A, 1)
@@ -101,36 +102,39 @@ def test_numeric_product_matches_oracle(name):
     ws = sp.Workspace.for_operands(dA, dB)
     for seed, ratio in ((0, 0.01), (1, 0.1)):
         cfg = sp.config(threshold=int(ratio * TWO32), seed=seed)
-        p = sp.numeric_product(dA, dav, dB, dbv, cfg, ws=ws)
-        o_rpt = _check_against_oracle(A, B, av, bv, p.rpt, p.col, p.val, f"{name} seed {seed}")
+        p = sp.numeric_product(dA, dav, dB, dbv, cfg, ws=ws, pool=pool)
+        o_rpt = _check_against_oracle(A, B, av, bv, p.rpt, p.col, p.val, f"{name} seed {seed} pool {pool}")
         info = p.info["numeric"]
         assert info["status"] == 0
         assert info["nnz_total"] == o_rpt[-1]
-        # overflow rows: exact nnz above the predicted share
         pred = sp.predict_structure(dA, dB, cfg, ws=ws)
-        share = np.diff(pred.offsets.cpu().numpy())
         exact = np.diff(o_rpt)
-        assert info["overflow_rows"] == int(np.sum(exact > share))
-        assert info["overflow_nnz"] == int(exact[exact > share].sum())
         assert info["alloc_total"] == int(pred.offsets[-1].item())
+        if not pool:  # overflow rows: exact nnz above the predicted share
+            share = np.diff(pred.offsets.cpu().numpy())
+            assert info["overflow_rows"] == int(np.sum(exact > share))
+            assert info["overflow_nnz"] == int(exact[exact > share].sum())
+        elif o_rpt[-1] <= info["alloc_total"]:  # a pool of at least NNZ(C) may still be cut by its stripes
+            assert info["overflow_nnz"] <= o_rpt[-1]
 
 
 def _into(dA, dav, dB, dbv, alloc, ws, cap=None):
-    total = int(alloc[-1].item())
-    cap = total if cap is None else cap
+    """Numeric pass into per-row shares (alloc) or, with alloc None, a pool of cap entries."""
+    cap = int(alloc[-1].item()) if cap is None else cap
     c_col = torch.full((max(cap, 1),), -7, dtype=torch.int32, device="cuda")[:cap]
     c_val = torch.zeros(max(cap, 1), dtype=torch.float32, device="cuda")[:cap]
+    row_start = torch.empty(dA.rows, dtype=torch.int64, device="cuda")
     nnz_row = torch.empty(dA.rows, dtype=torch.int32, device="cuda")
     res = sp.new_numeric_result()
-    assert sp.spgemm_numeric_into(dA, dav, dB, dbv, alloc, c_col, c_val, nnz_row, res, ws) == sp.OK
-    return c_col, c_val, nnz_row, res
+    assert sp.spgemm_numeric_into(dA, dav, dB, dbv, alloc, c_col, c_val, row_start, nnz_row, res, ws) == sp.OK
+    return c_col, c_val, row_start, nnz_row, res
 
 
-def _compact(dA, dav, dB, dbv, alloc, c_col, c_val, nnz_row, res, ws, Z):
+def _compact(dA, dav, dB, dbv, c_col, c_val, row_start, nnz_row, res, ws, Z):
     out_rpt = torch.empty(dA.rows + 1, dtype=torch.int64, device="cuda")
     out_col = torch.empty(max(Z, 1), dtype=torch.int32, device="cuda")[:Z]
     out_val = torch.empty(max(Z, 1), dtype=torch.float32, device="cuda")[:Z]
-    assert sp.spgemm_numeric_compact(dA, dav, dB, dbv, alloc, c_col, c_val, nnz_row, out_rpt, out_col, out_val,
+    assert sp.spgemm_numeric_compact(dA, dav, dB, dbv, c_col, c_val, row_start, nnz_row, out_rpt, out_col, out_val,
                                      res, ws) == sp.OK
     return out_rpt, out_col, out_val
 
@@ -155,18 +159,65 @@ def test_overflow_fallback(name, shrink):
     alloc_h = np.zeros(A.rows + 1, dtype=np.int64)
     np.cumsum(share, out=alloc_h[1:])
     alloc = torch.from_numpy(alloc_h).cuda()
-    c_col, c_val, nnz_row, res = _into(dA, dav, dB, dbv, alloc, ws)
+    c_col, c_val, row_start, nnz_row, res = _into(dA, dav, dB, dbv, alloc, ws)
     info = sp.read_numeric_result(res)
     assert np.array_equal(nnz_row.cpu().numpy(), exact)
     assert info["nnz_total"] == int(exact.sum()) and info["status"] == 0
     over = exact > share
     assert info["overflow_rows"] == int(over.sum()) and info["overflow_nnz"] == int(exact[over].sum())
+    rs = row_start.cpu().numpy()
+    assert np.array_equal(rs < 0, over) and np.array_equal(rs[~over], alloc_h[:-1][~over])
     if shrink in ("exact", "flop"):
         assert info["overflow_rows"] == 0
-    if shrink == "exact":  # the padded layout is the exact CSR already
+    if shrink == "exact":  # the layout is the exact CSR already
         _check_against_oracle(A, B, av, bv, alloc, c_col, c_val, f"{name} padded")
-    out = _compact(dA, dav, dB, dbv, alloc, c_col, c_val, nnz_row, res, ws, int(exact.sum()))
+    out = _compact(dA, dav, dB, dbv, c_col, c_val, row_start, nnz_row, res, ws, int(exact.sum()))
     _check_against_oracle(A, B, av, bv, *out, f"{name} {shrink}")
+    assert sp.read_numeric_result(res)["status"] == 0
+
+
+@pytest.mark.parametrize("name", ["er-16k", "rmat-12", "dense-blocks-64", "hubs"])
+@pytest.mark.parametrize("fill", [0.0, 0.3, 0.9, 1.0, 1.5])
+def test_pool_mode(name, fill):
+    """One pool of fill * NNZ(C) entries: rows take exactly their size while a
+    stripe has room; the rows written are disjoint, inside the pool, and hold
+    their exact entries; the others overflow; the compaction gives the exact
+    product every time."""
+    A, B = CASES[name]
+    B = A if B is None else B
+    av = _values(A, 11)
+    bv = av if B is A else _values(B, 12)
+    dA = to_dev(A)
+    dB = dA if B is A else to_dev(B)
+    dav = torch.from_numpy(av).cuda()
+    dbv = dav if B is A else torch.from_numpy(bv).cuda()
+    ws = sp.Workspace.for_operands(dA, dB)
+    exact = oracle.symbolic_exact(A, B)[0]
+    Z = int(exact.sum())
+    cap = int(fill * Z)
+    c_col, c_val, row_start, nnz_row, res = _into(dA, dav, dB, dbv, None, ws, cap=cap)
+    info = sp.read_numeric_result(res)
+    assert info["status"] == 0 and info["nnz_total"] == Z and info["alloc_total"] == cap
+    assert np.array_equal(nnz_row.cpu().numpy(), exact)
+    rs = row_start.cpu().numpy()
+    written = (rs >= 0) & (exact > 0)
+    assert info["overflow_rows"] == int(np.sum(rs < 0))
+    assert info["overflow_nnz"] == int(exact[rs < 0].sum())
+    assert np.all(rs[written] + exact[written] <= cap)
+    order = np.argsort(rs[written])
+    ends = (rs[written] + exact[written])[order]
+    assert np.all(ends[:-1] <= rs[written][order][1:])  # disjoint
+    if fill == 0.0:
+        assert np.all(rs[exact > 0] < 0)
+    # the written rows hold their exact entries
+    o_rpt, o_col, o_val, o_abs, o_terms = oracle.numeric(A, av, B, bv)
+    cc = c_col.cpu().numpy()
+    vv = c_val.cpu().numpy().astype(np.float64)
+    for i in np.nonzero(written)[0][:200]:
+        got = np.sort(cc[rs[i]:rs[i] + exact[i]])
+        assert np.array_equal(got, o_col[o_rpt[i]:o_rpt[i + 1]]), f"row {i}"
+    out = _compact(dA, dav, dB, dbv, c_col, c_val, row_start, nnz_row, res, ws, Z)
+    _check_against_oracle(A, B, av, bv, *out, f"{name} pool {fill}")
     assert sp.read_numeric_result(res)["status"] == 0
 
 
@@ -186,14 +237,16 @@ def test_short_arrays_make_rows_overflow_not_writes():
     guard = 4096
     big_col = torch.full((cap + guard,), -7, dtype=torch.int32, device="cuda")
     big_val = torch.full((cap + guard,), 123.0, dtype=torch.float32, device="cuda")
+    row_start = torch.empty(A.rows, dtype=torch.int64, device="cuda")
     nnz_row = torch.empty(A.rows, dtype=torch.int32, device="cuda")
     res = sp.new_numeric_result()
-    assert sp.spgemm_numeric_into(dA, dav, dA, dav, alloc, big_col[:cap], big_val[:cap], nnz_row, res, ws) == sp.OK
+    assert sp.spgemm_numeric_into(dA, dav, dA, dav, alloc, big_col[:cap], big_val[:cap], row_start, nnz_row, res,
+                                  ws) == sp.OK
     info = sp.read_numeric_result(res)
     fits = alloc_h[1:] <= cap
     assert info["overflow_rows"] == int((~fits & (exact > 0)).sum())
     assert np.all(big_col[cap:].cpu().numpy() == -7) and np.all(big_val[cap:].cpu().numpy() == 123.0)
-    out = _compact(dA, dav, dA, dav, alloc, big_col[:cap], big_val[:cap], nnz_row, res, ws, int(exact.sum()))
+    out = _compact(dA, dav, dA, dav, big_col[:cap], big_val[:cap], row_start, nnz_row, res, ws, int(exact.sum()))
     _check_against_oracle(A, A, av, av, *out, "short arrays")
 
 
@@ -221,8 +274,8 @@ def test_empty_and_degenerate():
     dA, dB = to_dev(Abad), to_dev(Bok)
     ws = sp.Workspace.for_operands(dA, dB)
     alloc = torch.tensor([0, 8, 16], dtype=torch.int64, device="cuda")
-    c_col, c_val, nnz_row, res = _into(dA, torch.ones(3, device="cuda"), dB,
-                                       torch.ones(Bok.nnz, device="cuda"), alloc, ws)
+    c_col, c_val, row_start, nnz_row, res = _into(dA, torch.ones(3, device="cuda"), dB,
+                                                  torch.ones(Bok.nnz, device="cuda"), alloc, ws)
     assert sp.read_numeric_result(res)["status"] & sp.STATUS_ERR_BAD_INPUT
 
 
@@ -234,7 +287,7 @@ def test_repeated_calls_reuse_the_workspace():
     ws = sp.Workspace.for_operands(dA, dA)
     first = None
     for k in range(4):
-        p = sp.numeric_product(dA, dav, dA, dav, sp.config(ratio=0.02, seed=k % 2), ws=ws)
+        p = sp.numeric_product(dA, dav, dA, dav, sp.config(ratio=0.02, seed=k % 2), ws=ws, pool=k % 2 == 0)
         rows = np.repeat(np.arange(A.rows), np.diff(p.rpt.cpu().numpy()))
         key = np.lexsort((p.col.cpu().numpy(), rows))
         got = (p.rpt.cpu().numpy(), p.col.cpu().numpy()[key])
