@@ -267,7 +267,7 @@ __device__ long long num_row_warp(const NumArgs& a, int row, int* keys, float* v
   // count, then write when the row fits its target
   int nnz = 0;
   for (int i0 = 0; i0 < P; i0 += 32) nnz += __popc(__ballot_sync(kFull, keys[i0 + lane] != -1));
-  NumTarget t;
+  NumTarget t{};
   if (lane == 0) t = num_target(a, row, nnz);
   t.dst = __shfl_sync(kFull, t.dst, 0);
   t.cap = __shfl_sync(kFull, t.cap, 0);
