@@ -24,6 +24,7 @@ constexpr int kWarpCap = kWarpTable / 2;      // products per row for the warp p
 constexpr int kHeavyThreads = 1024;           // threads per block of the heavy pass
 constexpr int kBlockHashCap = 16384;          // products per row for the block hash path
 constexpr int kBlockHashSlots = 2 * kBlockHashCap;
+constexpr int kHeavyUnroll = 8;               // products per lane loaded at once in the heavy pass
 
 enum RowSource { kSrcBernoulli = 0, kSrcDraws = 1, kSrcAllRows = 2 };
 
@@ -299,18 +300,33 @@ __device__ long long heavy_count_pass(const DedupArgs& a, long long rb, long lon
         if (sm.ex[mid] <= p) lo_i = mid; else hi_i = mid;
       }
       int o = lo_i;
-      for (; p < p_end; p += 32) {
-        while (o + 1 < nent && sm.ex[o + 1] <= p) ++o;
-        const int col = __ldg(a.b_col + sm.bs[o] + p);
-        if (BITMAP) {
-          if (col >= lo && col < hi) {
-            const long long off = col - lo;
-            atomicOr(&tab[off >> 5], 1u << (off & 31));
-          } else if ((unsigned)col >= (unsigned long long)a.N) {
-            bad = true;
+      // kHeavyUnroll column ids per lane are loaded before any is used, so
+      // that many loads of each lane are in flight at once
+      for (; p < p_end; p += 32 * kHeavyUnroll) {
+        int col[kHeavyUnroll];
+#pragma unroll
+        for (int u = 0; u < kHeavyUnroll; ++u) {
+          const long long pu = p + 32 * u;
+          col[u] = -1;
+          if (pu < p_end) {
+            while (o + 1 < nent && sm.ex[o + 1] <= pu) ++o;
+            col[u] = __ldg(a.b_col + sm.bs[o] + pu);
           }
-        } else {
-          cnt += table_insert(reinterpret_cast<int*>(tab), lg_or_words, col);
+        }
+#pragma unroll
+        for (int u = 0; u < kHeavyUnroll; ++u) {
+          if (p + 32 * u >= p_end) continue;
+          const int c = col[u];
+          if (BITMAP) {
+            if (c >= lo && c < hi) {
+              const long long off = c - lo;
+              atomicOr(&tab[off >> 5], 1u << (off & 31));
+            } else if ((unsigned)c >= (unsigned long long)a.N) {
+              bad = true;
+            }
+          } else {
+            cnt += table_insert(reinterpret_cast<int*>(tab), lg_or_words, c);
+          }
         }
       }
     }

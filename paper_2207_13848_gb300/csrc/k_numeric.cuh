@@ -42,6 +42,7 @@ constexpr int kNumBlockCap = kNumBlockSlots / 2;   // products per row for the b
 constexpr int kNumDenseCols = 49152;               // columns per dense pass (192 KB of values)
 constexpr int kNumDenseWords = kNumDenseCols / 32;  // its occupancy bitmap (6 KB)
 constexpr int kPoolStripes = 64;                   // pool mode: bump pointers (one per workspace slot)
+constexpr int kNumUnroll = 4;                      // block pass: products per lane loaded at once
 
 constexpr size_t kNumRowsSmem = (size_t)kNumWarps * kNumWarpSlots * (sizeof(int) + sizeof(float));
 constexpr size_t kNumBlockTableSmem = (size_t)kNumBlockSlots * (sizeof(int) + sizeof(float));
@@ -331,15 +332,31 @@ __device__ void num_block_products(const NumArgs& a, long long rb, long long re,
         if (sm.ex[mid] <= p) lo_i = mid; else hi_i = mid;
       }
       int o = lo_i;
-      for (; p < p_end; p += 32) {
-        while (o + 1 < nent && sm.ex[o + 1] <= p) ++o;
-        const long long q = sm.bs[o] + p;
-        const int col = __ldg(a.b_col + q);
-        if ((unsigned)col >= (unsigned long long)a.N) {
-          bad = true;
-          continue;
+      // kNumUnroll products per lane are loaded before any is used
+      for (; p < p_end; p += 32 * kNumUnroll) {
+        int col[kNumUnroll];
+        float pv[kNumUnroll];
+#pragma unroll
+        for (int u = 0; u < kNumUnroll; ++u) {
+          const long long pu = p + 32 * u;
+          col[u] = -1;
+          pv[u] = 0.0f;
+          if (pu < p_end) {
+            while (o + 1 < nent && sm.ex[o + 1] <= pu) ++o;
+            const long long q = sm.bs[o] + pu;
+            col[u] = __ldg(a.b_col + q);
+            if (VAL) pv[u] = sm.av[o] * __ldg(a.b_val + q);
+          }
         }
-        f(col, VAL ? sm.av[o] * __ldg(a.b_val + q) : 0.0f);
+#pragma unroll
+        for (int u = 0; u < kNumUnroll; ++u) {
+          if (p + 32 * u >= p_end) continue;
+          if ((unsigned)col[u] >= (unsigned long long)a.N) {
+            bad = true;
+            continue;
+          }
+          f(col[u], pv[u]);
+        }
       }
     }
     __syncthreads();
