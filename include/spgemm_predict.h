@@ -49,8 +49,8 @@ extern "C" {
 #define SPGEMM_ERR_WORKSPACE (-3)    /* ws_bytes < spgemm_workspace_size(A, B) */
 #define SPGEMM_ERR_CUDA (-4)         /* a CUDA launch or query failed */
 #define SPGEMM_ERR_TOO_LARGE (-5)    /* a size does not fit the int32 index range */
-#define SPGEMM_ERR_STATIC_CAPACITY (-6) /* spgemm_predict_structure_static: A.rows or A.cols
-                                           exceeds SPGEMM_STATIC_MAX_ROWS */
+#define SPGEMM_ERR_STATIC_CAPACITY (-6) /* spgemm_predict_structure_static: A.rows, A.cols or
+                                           B.cols exceeds SPGEMM_STATIC_MAX_ROWS */
 
 /* ---- device status bits (res->status) ------------------------------------------ */
 #define SPGEMM_STATUS_OK 0
@@ -114,9 +114,10 @@ typedef struct spgemm_result {
 
 /* ---- entry points ----------------------------------------------------------------- */
 
-/* Bytes of device workspace every entry point below needs for these operands
- * (about 8 * A.rows + A.cols bytes plus a fixed 263 KB).  B may be NULL; the
- * size depends on A's shape only. */
+/* Bytes of device workspace every entry point below needs for these operands:
+ * about 8 * A.rows + A.cols + 8 * B.cols bytes plus a fixed 268 KB (the B.cols
+ * part holds the bitmaps of sampled rows split over several thread blocks).  B
+ * may be NULL, in which case B.cols is taken to be A.cols (C = A * A). */
 size_t spgemm_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B);
 
 /* Algorithm 1 (Sec. V-A): flop_row[i] = sum over j in row i of A of
@@ -190,20 +191,21 @@ int spgemm_set_profile_events(void* before, void* after);
  * cudaMalloc because that call can synchronise the whole device.
  *
  * The scratch space is a fixed array of device memory compiled into the library,
- * sized for A.rows <= SPGEMM_STATIC_MAX_ROWS and A.cols <= SPGEMM_STATIC_MAX_ROWS
- * (about 19 MB).  Every GPU that loads the library holds it until the process
- * exits.  Larger problems are rejected
- * with SPGEMM_ERR_STATIC_CAPACITY before anything is queued.  The call allocates
+ * sized for A.rows, A.cols and B.cols <= SPGEMM_STATIC_MAX_ROWS (about 35 MB).
+ * Every GPU that loads the library holds it until the process exits.  Larger
+ * problems are rejected with SPGEMM_ERR_STATIC_CAPACITY before anything is
+ * queued.  The call allocates
  * nothing (no cudaMalloc/cudaFree, no allocating library routine): the caller
  * still passes the inputs, outputs and result record, as for
  * spgemm_predict_structure, and gets the same results.
  *
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array and clears its bookkeeping part
- * (262 KB, a cudaMemsetAsync on `stream`) before use, so calls that overlap on
- * the GPU (on different streams, or from several threads) race and must not be
- * issued. */
+ * capture.  Every call shares the one array and clears its bookkeeping parts
+ * (the 262 KB header and block slots, 4 * A.rows bytes of row queue and the
+ * split-row slots; cudaMemsetAsync on `stream`) before use, so calls that
+ * overlap on the GPU (on different streams, or from several threads) race and
+ * must not be issued. */
 #define SPGEMM_STATIC_MAX_ROWS (1ll << 21)
 int spgemm_predict_structure_static(const spgemm_csr_t* A, const spgemm_csr_t* B,
                                     const spgemm_config_t* cfg, int32_t* pred_row,

@@ -149,7 +149,7 @@ int check_pair(const spgemm_csr_t* A, const spgemm_csr_t* B, void* ws, size_t ws
   if (!csr_ok(A) || !csr_ok(B) || !res || !ws) return SPGEMM_ERR_INVALID_ARG;
   if (A->cols != B->rows) return SPGEMM_ERR_DIM_MISMATCH;
   if (!csr_fits(A) || !csr_fits(B)) return SPGEMM_ERR_TOO_LARGE;
-  if (ws_bytes < ws_bytes_for(A->rows, A->cols)) return SPGEMM_ERR_WORKSPACE;
+  if (ws_bytes < ws_bytes_for(A->rows, A->cols, B->cols)) return SPGEMM_ERR_WORKSPACE;
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return SPGEMM_ERR_WORKSPACE;
   return SPGEMM_OK;
 }
@@ -301,7 +301,7 @@ int predict_common(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_co
   const DeviceLimits* L = limits();
   if (!L) return SPGEMM_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Workspace w = ws_carve(ws, A->rows);
+  Workspace w = ws_carve(ws, A->rows, A->cols, B->cols);
   DedupArgs d = dedup_args(A, B, w);
   d.src = cfg->mode == SPGEMM_SAMPLE_BERNOULLI ? kSrcBernoulli : kSrcDraws;
   d.seed = cfg->seed;
@@ -323,7 +323,9 @@ int predict_common(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_co
 constexpr size_t kStaticHeaderBytes = sizeof(WsHeader) + sizeof(Slot) * kMaxSlots;
 constexpr size_t kStaticRowBytes = ((size_t)SPGEMM_STATIC_MAX_ROWS * 4 + 255) / 256 * 256;
 constexpr size_t kStaticDegBytes = ((size_t)SPGEMM_STATIC_MAX_ROWS + 16 + 255) / 256 * 256;
-constexpr size_t kStaticBytes = kStaticHeaderBytes + 2 * kStaticRowBytes + kStaticDegBytes;
+constexpr size_t kStaticHugeBytes =
+    sizeof(HugeSlot) * kHugeSlots + (size_t)kHugeSlots * kMaxParts * ((size_t)SPGEMM_STATIC_MAX_ROWS + 2047) / 2048 * 64 * 4;
+constexpr size_t kStaticBytes = kStaticHeaderBytes + 2 * kStaticRowBytes + kStaticDegBytes + kStaticHugeBytes;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 void* g_static_ptr[kMaxDevices];
@@ -670,7 +672,7 @@ extern "C" {
 size_t spgemm_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B) {
   (void)B;
   if (!A || A->rows < 0) return 0;
-  return ws_bytes_for(A->rows, A->cols);
+  return ws_bytes_for(A->rows, A->cols, B ? B->cols : A->cols);
 }
 
 int spgemm_flop_per_row(const spgemm_csr_t* A, const spgemm_csr_t* B, int32_t* flop_row,
@@ -817,9 +819,16 @@ int spgemm_predict_structure_static(const spgemm_csr_t* A, const spgemm_csr_t* B
   std::call_once(g_static_once[dev], init_static_scratch, dev);
   void* ws = g_static_ptr[dev];
   if (!ws) return SPGEMM_ERR_CUDA;
-  if (ws_bytes_for(A->rows, A->cols) > kStaticBytes) return SPGEMM_ERR_STATIC_CAPACITY;
-  // Header, per-block slots and flag epoch start from zero on every call.
-  if (cudaMemsetAsync(ws, 0, kStaticHeaderBytes, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+  if (!csr_ok(B) || B->cols > SPGEMM_STATIC_MAX_ROWS) return B && csr_ok(B) ? SPGEMM_ERR_STATIC_CAPACITY : SPGEMM_ERR_INVALID_ARG;
+  if (ws_bytes_for(A->rows, A->cols, B->cols) > kStaticBytes) return SPGEMM_ERR_STATIC_CAPACITY;
+  // Header, per-block slots and flag epoch, the heavy-row queue and the
+  // split-row slots start from zero on every call (a call that ended with an
+  // error may have left them dirty).
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Workspace w = ws_carve(ws, A->rows, A->cols, B->cols);
+  if (cudaMemsetAsync(ws, 0, kStaticHeaderBytes, st) != cudaSuccess ||
+      cudaMemsetAsync(w.heavy, 0, (size_t)(A->rows > 0 ? A->rows : 1) * sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(w.huge, 0, sizeof(HugeSlot) * kHugeSlots, st) != cudaSuccess)
     return SPGEMM_ERR_CUDA;
   return predict_common(A, B, cfg, pred_row, offsets, flop_row, res, ws, kStaticBytes, stream, false);
 }
@@ -955,7 +964,7 @@ const char* spgemm_status_string(int code) {
     case SPGEMM_ERR_CUDA: return "CUDA launch or query failed";
     case SPGEMM_ERR_TOO_LARGE: return "size exceeds the int32 index range";
     case SPGEMM_ERR_STATIC_CAPACITY:
-      return "A.rows or A.cols exceeds the static scratch of spgemm_predict_structure_static (SPGEMM_STATIC_MAX_ROWS)";
+      return "A.rows, A.cols or B.cols exceeds the static scratch of spgemm_predict_structure_static (SPGEMM_STATIC_MAX_ROWS)";
     case SPGEMM_STATUS_WARN_EMPTY_SAMPLE: return "warning: empty sample, prediction fell back to FLOP";
     case SPGEMM_STATUS_WARN_SATURATED: return "warning: a prediction saturated at 2^31-1";
     case SPGEMM_STATUS_WARN_UNSORTED: return "warning: a row is not strictly increasing";

@@ -56,27 +56,48 @@ struct alignas(64) Slot {
   long long pad1;
 };
 
+// A sampled row with very many products is split by its entries into parts
+// that several blocks count at once, each into a shared-memory bitmap over B's
+// columns that it writes out whole to its own bitmap in the workspace; the
+// block that finishes the row's last part ORs the parts' bitmaps and counts.
+constexpr int kHugeSlots = 8;    // split rows in progress at once
+constexpr int kMaxParts = 8;     // parts of one split row
+struct alignas(64) HugeSlot {
+  unsigned int state;       // 0 free, 1 being set up, 2 parts claimable
+  unsigned int parts;       // number of parts
+  unsigned int part_ctr;    // parts claimed (parked high while being set up)
+  unsigned int parts_done;  // parts counted
+  long long bnd[kMaxParts + 1];  // part p = A entries [bnd[p], bnd[p + 1])
+};
+
 struct Workspace {
   WsHeader* hdr;
   Slot* slots;
   int* heavy;            // [M] rows queued for the block-per-row deduplication
   int* flop_buf;         // [M] per-row FLOP when the caller gives no flop_row buffer
   unsigned char* deg8;   // [K] B row lengths capped at kDegEscape (see k_degree_table)
+  HugeSlot* huge;        // [kHugeSlots] split rows (when carved with N > 0)
+  unsigned int* hbits;   // [kHugeSlots][kMaxParts][huge_words] the parts' bitmaps over B's columns
+  long long huge_words;  // words of one bitmap (0 when not carved)
 };
 
 // B row lengths of at least kDegEscape are read from B.rpt instead of the table.
 constexpr int kDegEscape = 255;
 
 inline size_t ws_round(size_t b) { return ((b + 255) / 256) * 256; }
+inline long long ws_huge_words(int64_t N) { return N > 0 ? (N + 2047) / 2048 * 64 : 0; }
 
-// Bytes for M rows of A and K columns of A (= rows of B).
-inline size_t ws_bytes_for(int64_t M, int64_t K) {
+// Bytes for M rows of A, K columns of A (= rows of B) and N columns of B (the
+// split-row bitmaps; N = 0 leaves them out).
+inline size_t ws_bytes_for(int64_t M, int64_t K, int64_t N = 0) {
   const size_t m = (size_t)(M > 0 ? M : 1), k = (size_t)(K > 0 ? K : 1);
-  return sizeof(WsHeader) + sizeof(Slot) * kMaxSlots + 2 * ws_round(m * 4) + ws_round(k + 16);
+  size_t b = sizeof(WsHeader) + sizeof(Slot) * kMaxSlots + 2 * ws_round(m * 4) + ws_round(k + 16);
+  if (N > 0) b += sizeof(HugeSlot) * kHugeSlots + (size_t)kHugeSlots * kMaxParts * (size_t)ws_huge_words(N) * 4;
+  return b;
 }
 
-inline Workspace ws_carve(void* base, int64_t M) {
-  const size_t m = (size_t)(M > 0 ? M : 1);
+inline Workspace ws_carve(void* base, int64_t M, int64_t K = 0, int64_t N = 0) {
+  const size_t m = (size_t)(M > 0 ? M : 1), k = (size_t)(K > 0 ? K : 1);
   char* p = static_cast<char*>(base);
   Workspace w;
   w.hdr = reinterpret_cast<WsHeader*>(p);
@@ -88,6 +109,11 @@ inline Workspace ws_carve(void* base, int64_t M) {
   w.flop_buf = reinterpret_cast<int*>(p);
   p += ws_round(m * 4);
   w.deg8 = reinterpret_cast<unsigned char*>(p);
+  p += ws_round(k + 16);
+  w.huge = N > 0 ? reinterpret_cast<HugeSlot*>(p) : nullptr;
+  p += sizeof(HugeSlot) * kHugeSlots;
+  w.hbits = N > 0 ? reinterpret_cast<unsigned int*>(p) : nullptr;
+  w.huge_words = ws_huge_words(N);
   return w;
 }
 

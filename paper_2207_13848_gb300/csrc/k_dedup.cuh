@@ -272,7 +272,7 @@ struct HeavySmem {
   long long red[kHeavyThreads / 32 + 1];
 };
 
-template <bool BITMAP>
+template <bool BITMAP, bool COUNT = true>
 __device__ long long heavy_count_pass(const DedupArgs& a, long long rb, long long re, HeavySmem& sm,
                                       unsigned* tab, int lg_or_words, long long lo, long long hi,
                                       bool& bad) {
@@ -332,6 +332,7 @@ __device__ long long heavy_count_pass(const DedupArgs& a, long long rb, long lon
     }
     __syncthreads();
   }
+  if (!COUNT) return 0;  // bitmap left in tab for the caller
   if (BITMAP) {
     for (int i = t; i < lg_or_words; i += kHeavyThreads) cnt += __popc(tab[i]);
   }
@@ -341,19 +342,26 @@ __device__ long long heavy_count_pass(const DedupArgs& a, long long rb, long lon
 // Exact nnz of one heavy row by the whole block (kHeavyThreads threads): a
 // shared hash table when the row has at most kBlockHashCap products, else a
 // bitmap over B's columns, one column range of bitmap_words * 32 at a time.
-__device__ long long heavy_row_nnz(const DedupArgs& a, int row, HeavySmem& sm, unsigned* tab,
-                                   int bitmap_words, bool& bad, long long* flop_out = nullptr) {
+// The row's A entry range [*rb, *re) and its FLOP, by the whole block.
+__device__ long long heavy_row_flop(const DedupArgs& a, int row, HeavySmem& sm, long long* rb_out,
+                                    long long* re_out, bool& bad) {
   long long rb = __ldg(a.a_rpt + row), re = __ldg(a.a_rpt + row + 1);
   if (!clamp_range(rb, re, a.nnzA)) bad = true;
-  // the row's FLOP decides the method
   long long fl = 0;
   for (long long j = rb + threadIdx.x; j < re; j += kHeavyThreads) {
     long long s, len;
     b_row(a, __ldg(a.a_col + j), s, len, bad);
     fl += len;
   }
-  const long long flop = block_sum<kHeavyThreads>(fl, sm.red);
-  if (flop_out) *flop_out = flop;
+  *rb_out = rb;
+  *re_out = re;
+  return block_sum<kHeavyThreads>(fl, sm.red);
+}
+
+// Exact nnz of the row whose entries are [rb, re) and FLOP is flop, by the
+// whole block (see heavy_row_nnz).
+__device__ long long heavy_row_count(const DedupArgs& a, long long rb, long long re, long long flop,
+                                     HeavySmem& sm, unsigned* tab, int bitmap_words, bool& bad) {
   long long nnz = 0;
   if (flop <= kBlockHashCap) {
     const int lg = ceil_log2((uint32_t)(2 * flop));
@@ -371,6 +379,14 @@ __device__ long long heavy_row_nnz(const DedupArgs& a, int row, HeavySmem& sm, u
     }
   }
   return nnz;
+}
+
+__device__ long long heavy_row_nnz(const DedupArgs& a, int row, HeavySmem& sm, unsigned* tab,
+                                   int bitmap_words, bool& bad, long long* flop_out = nullptr) {
+  long long rb, re;
+  const long long flop = heavy_row_flop(a, row, sm, &rb, &re, bad);
+  if (flop_out) *flop_out = flop;
+  return heavy_row_count(a, rb, re, flop, sm, tab, bitmap_words, bad);
 }
 
 __global__ void __launch_bounds__(kHeavyThreads) k_dedup_heavy(DedupArgs a, int bitmap_words) {

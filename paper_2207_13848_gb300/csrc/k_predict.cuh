@@ -118,7 +118,8 @@ struct PredStatic {
   unsigned long long pre[4];         // f*, z*, |S| and the ratio's reciprocal, read early
   int pre_ready;                     // 1: pre[] is final and no sampled row is heavy
   int stream_fin;                    // the streaming group has finished its FLOP pass
-  int s_enc;
+  int s_enc, s_part;
+  int s_last;
   int list[kListCapW];
   HeavySmem heavy;
 };
@@ -420,6 +421,189 @@ __device__ int claim_heavy_row(WsHeader* hdr, int* heavy, unsigned long long cap
   return 0;
 }
 
+// ---- split rows ------------------------------------------------------------------
+constexpr long long kHugeProducts = 1ll << 20;  // sampled rows with more products are split
+constexpr long long kPartProducts = 1ll << 17;  // products per part, at least
+constexpr unsigned kPartParked = 0xffff0000u;   // part_ctr while a slot is being set up
+
+// Thread 0: claims a part of a split row; returns slot * 128 + part, or -1.
+__device__ int claim_part(HugeSlot* hs) {
+  for (int s = 0; s < kHugeSlots; ++s) {
+    if (flag_load(&hs[s].state) != 2u) continue;
+    volatile HugeSlot* v = hs + s;
+    if (v->part_ctr >= v->parts) continue;
+    const unsigned q = atomicAdd(&hs[s].part_ctr, 1u);
+    __threadfence();
+    // the slot may have been finished and set up again in between: the claim
+    // counts only against the row now published there
+    if (flag_load(&hs[s].state) == 2u && q < v->parts) return s * 128 + (int)q;
+  }
+  return -1;
+}
+
+// The whole block: sets up slot h for a row with entries [rb, re) and FLOP
+// flop > kHugeProducts: up to kMaxParts parts of about equal products (at
+// least kPartProducts each), cut at entry starts.
+__device__ void split_row(const DedupArgs& d, HugeSlot* h, long long rb, long long re, long long flop,
+                          long long* red, bool& bad) {
+  const int t = threadIdx.x;
+  const long long ps = max(kPartProducts, (flop + kMaxParts - 1) / kMaxParts);
+  const int P = (int)min((long long)kMaxParts, (flop + ps - 1) / ps);
+  long long pre = 0;
+  for (long long g = rb; g < re; g += kPredThreads) {
+    long long st = 0, len = 0;
+    if (g + t < re) b_row(d, __ldg(d.a_col + g + t), st, len, bad);
+    long long tot;
+    const long long ex = block_excl_scan<kPredThreads>(len, red, &tot) + pre;
+    // part k >= 1 starts at the entry whose products hold product k * ps
+    if (len > 0) {
+      for (long long k = max(1ll, (ex + ps - 1) / ps); k < P && k * ps < ex + len; ++k) h->bnd[k] = g + t;
+    }
+    pre += tot;
+  }
+  __threadfence();  // each writer's boundaries are visible before the slot is published
+  __syncthreads();
+  if (t == 0) {
+    h->bnd[0] = rb;
+    h->bnd[P] = re;
+    h->parts = (unsigned)P;
+    h->parts_done = 0;
+    __threadfence();
+    h->part_ctr = 0;
+    __threadfence();
+    flag_store(&h->state, 2u);
+  }
+}
+
+// The heavy sampled rows, by the whole block: parts of split rows first, then
+// rows from the queue (rows with more than kHugeProducts products are split
+// into parts for all blocks), until every queued row is counted.  Returns
+// whether the FLOP of the block's rows is still in sflop (the tables used
+// here overwrite it, so it is moved to f.flop before the first one).  Kept
+// out of line so that its registers do not weigh on the FLOP pass.
+__device__ __noinline__ bool heavy_phase(const PredArgs& p, PredStatic& ss, unsigned char* pdyn, int* sflop,
+                                         int i0, int i1) {
+  const FlopArgs& a = p.f;
+  const DedupArgs& d = p.d;
+  const int t = threadIdx.x;
+  const int G = gridDim.x;
+  WsHeader* hdr = a.ws.hdr;
+  bool flop_in_smem = true;
+  unsigned* tab = reinterpret_cast<unsigned*>(pdyn);
+  HugeSlot* hs = a.ws.huge;
+  const uint64_t t_start = global_ns();
+  for (;;) {
+    if (t == 0) {
+      ss.s_part = hs ? claim_part(hs) : -1;
+      ss.s_enc = ss.s_part >= 0 ? 0 : claim_heavy_row(hdr, d.heavy, (unsigned long long)d.heavy_cap, (unsigned)G);
+    }
+    __syncthreads();
+    const int part = ss.s_part, enc = ss.s_enc;
+    if ((part >= 0 || enc != 0) && flop_in_smem) {  // the tables below overwrite sflop: move it out first
+      if (!p.flop_out)
+        for (int r = i0 + t; r < min(i1, (i0 & ~3) + kSFlopN); r += kPredThreads) a.flop[r] = sflop[r - (i0 & ~3)];
+      flop_in_smem = false;
+      __syncthreads();
+    }
+    bool bad = false;
+    if (part >= 0) {
+      // ---- one part of a split row: its bitmap over B's columns, written whole
+      HugeSlot* h = hs + (part >> 7);
+      const int q = part & 127;
+      unsigned* gb = a.ws.hbits + ((long long)(part >> 7) * kMaxParts + q) * a.ws.huge_words;
+      const long long rb = *reinterpret_cast<volatile long long*>(&h->bnd[q]);
+      const long long re = *reinterpret_cast<volatile long long*>(&h->bnd[q + 1]);
+      const long long range = (long long)p.bitmap_words * 32;
+      for (long long lo = 0; lo < d.N; lo += range) {
+        const long long hi = min((long long)d.N, lo + range);
+        const int words = (int)((hi - lo + 31) / 32);
+        for (int i = t; i < words; i += kPredThreads) tab[i] = 0u;
+        __syncthreads();
+        heavy_count_pass<true, false>(d, rb, re, ss.heavy, tab, words, lo, hi, bad);
+        for (int i = t; i < words; i += kPredThreads) gb[(lo >> 5) + i] = tab[i];
+        __threadfence();  // every thread's words are visible before the part counts as done
+        __syncthreads();
+      }
+      if (t == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&h->parts_done, 1u);
+        ss.s_last = prev + 1 == *reinterpret_cast<volatile unsigned*>(&h->parts);
+      }
+      __syncthreads();
+      if (ss.s_last) {  // the row's last part: OR the parts' bitmaps, count, free the slot
+        __threadfence();
+        const unsigned nparts = *reinterpret_cast<volatile unsigned*>(&h->parts);
+        const unsigned* b0 = a.ws.hbits + (long long)(part >> 7) * kMaxParts * a.ws.huge_words;
+        long long cnt = 0;
+        const long long nw = (d.N + 31) / 32;
+        for (long long i = t; i < nw; i += kPredThreads) {
+          unsigned w = 0;
+          for (unsigned pp = 0; pp < nparts; ++pp) w |= __ldcg(b0 + pp * a.ws.huge_words + i);
+          cnt += __popc(w);
+        }
+        cnt = block_sum<kPredThreads>(cnt, ss.red);  // every read done before the slot is freed
+        if (t == 0) {
+          atomicAdd(&hdr->z_acc, (unsigned long long)cnt);
+          __threadfence();
+          // part_ctr stays at or above `parts`, so a late claim of this row
+          // fails; the next owner parks and resets it
+          flag_store(&h->state, 0u);
+          atomicAdd(&hdr->heavy_done, 1u);
+        }
+      }
+    } else if (enc != 0) {
+      // ---- a queued row: counted here, or split for all blocks
+      long long rb, re;
+      const int row = enc > 0 ? enc - 1 : -enc - 1;
+      const long long flop = heavy_row_flop(d, row, ss.heavy, &rb, &re, bad);
+      if (t == 0) {
+        if (enc < 0) atomicAdd(&hdr->f_acc, (unsigned long long)flop);
+        ss.s_part = -1;
+        if (hs && flop > kHugeProducts) {
+          for (int sl = 0; sl < kHugeSlots; ++sl) {
+            if (atomicCAS(&hs[sl].state, 0u, 1u) == 0u) {
+              hs[sl].part_ctr = kPartParked;
+              __threadfence();
+              ss.s_part = sl;
+              break;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (ss.s_part >= 0) {
+        split_row(d, hs + ss.s_part, rb, re, flop, ss.red, bad);
+      } else {  // small enough, or every split slot is taken: counted here
+        const long long nnz = heavy_row_count(d, rb, re, flop, ss.heavy, tab, p.bitmap_words, bad);
+        if (t == 0) {
+          atomicAdd(&hdr->z_acc, (unsigned long long)nnz);
+          __threadfence();
+          atomicAdd(&hdr->heavy_done, 1u);
+        }
+      }
+    } else {
+      // ---- nothing to take: leave once every queued row is counted (the
+      // parts of split rows still open are taken by the blocks at them)
+      if (t == 0) {
+        const unsigned nh = (unsigned)min((unsigned long long)flag_load(&hdr->heavy_count),
+                                          (unsigned long long)d.heavy_cap);
+        ss.s_last = flag_load(&hdr->heavy_done) >= nh;
+        if (!ss.s_last) {
+          __nanosleep(128);
+          if (global_ns() - t_start > 1000000000ull) {
+            atomicOr(&hdr->status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);
+            ss.s_last = 1;
+          }
+        }
+      }
+      __syncthreads();
+      if (ss.s_last) break;
+    }
+    if (__syncthreads_or(bad) && t == 0) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
+  }
+  return flop_in_smem;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
   static_assert(MODE == kModePredict || MODE == kModeReference, "prediction modes only");
@@ -561,34 +745,8 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
   // no sampled row is heavy anywhere, and f*, z*, |S| are already known
   const bool pre = ss.pre_ready == 1;
 
-  // ---- heavy sampled rows, one at a time, by the whole block
-  bool flop_in_smem = true;  // the FLOP of rows [i0, (i0 & ~3) + kSFlopN) is in sflop
-  {
-    unsigned* tab = reinterpret_cast<unsigned*>(pdyn);
-    while (!pre) {
-      if (t == 0) ss.s_enc = claim_heavy_row(hdr, d.heavy, (unsigned long long)d.heavy_cap, (unsigned)G);
-      __syncthreads();
-      const int enc = ss.s_enc;
-      if (enc == 0) break;
-      if (flop_in_smem) {  // the table below overwrites sflop: move it to f.flop first
-        if (!p.flop_out)
-          for (int r = i0 + t; r < min(i1, (i0 & ~3) + kSFlopN); r += kPredThreads) a.flop[r] = sflop[r - (i0 & ~3)];
-        flop_in_smem = false;
-        __syncthreads();
-      }
-      const int row = enc > 0 ? enc - 1 : -enc - 1;
-      bool bad = false;
-      long long flop = 0;
-      const long long nnz = heavy_row_nnz(d, row, ss.heavy, tab, p.bitmap_words, bad, &flop);
-      if (t == 0) {
-        atomicAdd(&hdr->z_acc, (unsigned long long)nnz);
-        if (enc < 0) atomicAdd(&hdr->f_acc, (unsigned long long)flop);
-        __threadfence();
-        atomicAdd(&hdr->heavy_done, 1u);
-      }
-      if (__syncthreads_or(bad) && t == 0) set_status(hdr, SPGEMM_STATUS_ERR_BAD_INPUT);
-    }
-  }
+  // ---- heavy sampled rows, by the whole block (none when `pre`)
+  const bool flop_in_smem = pre ? true : heavy_phase(p, ss, pdyn, sflop, i0, i1);
 
   // ---- predictions and offsets of the rows [i0, i1)
   if (t == 0) {

@@ -92,8 +92,10 @@ def _call_predict(lib, A, B, cfg, ws_bytes, res=0x3000, ws=0x10000, pred=0x4000,
 def test_host_errors(lib):
     A, B = _Fake(100, 50, 300), _Fake(50, 70, 200)
     cfg = sp.config(ratio=0.01)
-    need = sp.CsrStruct(100, 0, 0, 0, 0)
-    ws = lib.spgemm_workspace_size(ctypes.byref(need), None)
+    a, b = A.struct(), B.struct()
+    ws = lib.spgemm_workspace_size(ctypes.byref(a), ctypes.byref(b))
+    assert ws > lib.spgemm_workspace_size(ctypes.byref(sp.CsrStruct(100, 50, 0, 0, 0)),
+                                          ctypes.byref(sp.CsrStruct(50, 0, 0, 0, 0)))  # B.cols counts
     assert _call_predict(lib, A, _Fake(51, 70, 200), cfg, ws) == sp.ERR_DIM_MISMATCH
     assert _call_predict(lib, A, B, cfg, ws - 1) == sp.ERR_WORKSPACE
     assert _call_predict(lib, A, B, cfg, ws, ws=0x10010) == sp.ERR_WORKSPACE  # misaligned
