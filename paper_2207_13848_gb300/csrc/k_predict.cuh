@@ -938,36 +938,16 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
   long long ppart = 0;
   for (int q = t; q < c; q += kPredThreads) ppart += slot_total(&slots[q], ep, &hdr->status);
   const long long before = block_sum<kPredThreads>(ppart, ss.red);  // predicted nnz of blocks 0 .. c-1
-  // pass 2: the offsets (with the predictions, for a block of more chunks)
-  if (early) {
-#pragma unroll
-    for (int ch = 0; ch < kScanChunks; ++ch) {
-      if (ch < nchunks) {
-        const int r0 = base0 + ch * kChunkRows + t * kRowsPerThread;
-        int v[kRowsPerThread];
-        load_rows(r0, v);
-        store_offsets(r0, v, before + ex_c[ch]);
-      }
-    }
-  } else {
-    long long run = before;
-    for (int rb = base0; rb < i1; rb += kChunkRows) {
-      const int r0 = rb + t * kRowsPerThread;
-      int v[kRowsPerThread];
-      long long tot;
-      const long long ex = block_excl_scan<kPredThreads>(load_rows(r0, v), ss.red, &tot) + run;
-      store_pred(r0, v);
-      store_offsets(r0, v, ex);
-      run += tot;
-    }
-  }
   if (c == G - 1 && t == 0) {
     a.offsets[a.M] = before + blk_p;
     a.res->pred_total = before + blk_p;
   }
+  // every status bit of this block is set by now (saturation comes from pass 1)
   if (__syncthreads_or(sat) && t == 0) set_status(hdr, SPGEMM_STATUS_WARN_SATURATED);
 
-  // ---- the last block to finish writes the result record and resets the header
+  // ---- the block is done with the header and the other blocks' slots: the
+  // last block to get here writes the result record and resets the header
+  // while the blocks store their offsets
   if (t == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(&hdr->done, 1u);
@@ -995,6 +975,29 @@ __global__ void __launch_bounds__(kPredThreads, 1) k_predict(PredArgs p) {
       vh->done = 0;
       __threadfence();
       vh->epoch = ep;
+    }
+  }
+  // pass 2: the offsets (with the predictions, for a block of more chunks)
+  if (early) {
+#pragma unroll
+    for (int ch = 0; ch < kScanChunks; ++ch) {
+      if (ch < nchunks) {
+        const int r0 = base0 + ch * kChunkRows + t * kRowsPerThread;
+        int v[kRowsPerThread];
+        load_rows(r0, v);
+        store_offsets(r0, v, before + ex_c[ch]);
+      }
+    }
+  } else {
+    long long run = before;
+    for (int rb = base0; rb < i1; rb += kChunkRows) {
+      const int r0 = rb + t * kRowsPerThread;
+      int v[kRowsPerThread];
+      long long tot;
+      const long long ex = block_excl_scan<kPredThreads>(load_rows(r0, v), ss.red, &tot) + run;
+      store_pred(r0, v);
+      store_offsets(r0, v, ex);
+      run += tot;
     }
   }
 }
