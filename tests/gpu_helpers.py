@@ -4,6 +4,7 @@ import numpy as np
 
 import oracle
 import paper_2207_13848_gb300 as sp
+import workloads as W
 
 TWO32 = 1 << 32
 
@@ -19,6 +20,20 @@ def gpu_predict(A, B, mode, seed, threshold=0, sample_num=0, reference=False, ws
     p = sp.predict_structure(dA, dB, cfg, ws=ws, want_flop=True, reference=reference)
     return dict(pred=p.pred.cpu().numpy(), offsets=p.offsets.cpu().numpy(), flop=p.flop.cpu().numpy(),
                 **sp.read_result(p.res))
+
+
+def wide_hubs(M, K, N, n_hubs, hub_len, row_len, seed):
+    """A (M x K): rows 0..n_hubs-1 with hub_len entries, the others 3; B (K x N)
+    with row_len entries per row over all N columns: hub rows of hub_len *
+    row_len products."""
+    rng = np.random.default_rng(seed)
+    ra = [np.full(hub_len, i) for i in range(n_hubs)] + [np.repeat(np.arange(n_hubs, M), 3)]
+    ca = [rng.choice(K, size=hub_len, replace=False) for _ in range(n_hubs)] + \
+         [rng.integers(0, K, size=3 * (M - n_hubs))]
+    A = W.from_coo(M, K, np.concatenate(ra), np.concatenate(ca))
+    rb = np.repeat(np.arange(K), row_len)
+    cb = rng.integers(0, N, size=K * row_len)
+    return A, W.from_coo(K, N, rb, cb)
 
 
 def oracle_predict(A, B, mode, seed, threshold=0, sample_num=0, reference=False):

@@ -9,7 +9,7 @@ import pytest
 
 import paper_2207_13848_gb300 as sp
 import workloads as W
-from tests.gpu_helpers import TWO32, assert_prediction_equal, oracle_predict
+from tests.gpu_helpers import TWO32, assert_prediction_equal, oracle_predict, wide_hubs
 
 pytestmark = pytest.mark.gpu
 
@@ -110,6 +110,32 @@ def test_batch_edge_cases_match_oracle():
     for c, g in zip(cases, _batch_outputs(batch)):
         o = oracle_predict(c["A"], c["B"], c["mode"], c["seed"], c["threshold"], c["sample_num"])
         assert_prediction_equal(g, o, c["name"])
+
+
+def test_batch_split_rows_match_oracle():
+    # sampled hub rows of 1.3-1.5 M products (a whole block each, over B's
+    # columns in a shared-memory bitmap): 12 + 4 + 2 of them, one case with B
+    # wider than one bitmap pass, one with few columns (many duplicate
+    # products), among ordinary cases; run after run on one workspace
+    cases = [
+        dict(_case(W.erdos_renyi(4096, 8, 71), None, ratio=0.05, seed=1), name="er 4096"),
+        dict(_case(*wide_hubs(300, 3000, 1 << 20, 12, 2500, 600, seed=61), threshold=TWO32, seed=2),
+             name="12 hubs, N 2^20"),
+        dict(_case(W.rmat(13, 16, seed=72), None, seed=3), name="rmat 2^13"),
+        dict(_case(*wide_hubs(300, 3000, 5000, 4, 2500, 600, seed=62), threshold=TWO32, seed=4),
+             name="4 hubs, N 5000"),
+        dict(_case(*wide_hubs(200, 2800, (1 << 21) + 37, 2, 2600, 500, seed=63), threshold=TWO32, seed=5),
+             name="2 hubs, N 2^21 + 37"),
+    ]
+    for c in cases:
+        if c["B"] is None:
+            c["B"] = c["A"]
+    batch = sp.Batch(_device_cases(cases), want_flop=True)
+    want = [oracle_predict(c["A"], c["B"], c["mode"], c["seed"], c["threshold"], c["sample_num"]) for c in cases]
+    for rep in range(3):
+        batch.run()
+        for c, g, o in zip(cases, _batch_outputs(batch), want):
+            assert_prediction_equal(g, o, f"{c['name']} run {rep}")
 
 
 TUNINGS = [

@@ -12,7 +12,7 @@ import pytest
 import oracle
 import paper_2207_13848_gb300 as sp
 import workloads as W
-from tests.gpu_helpers import TWO32, assert_prediction_equal, gpu_predict, oracle_predict
+from tests.gpu_helpers import TWO32, assert_prediction_equal, gpu_predict, oracle_predict, wide_hubs
 
 pytestmark = pytest.mark.gpu
 
@@ -80,25 +80,11 @@ def test_hub_rows_repeated_calls_reuse_the_workspace():
         assert_prediction_equal(g, o, "repeat")
 
 
-def _wide_hubs(M, K, N, n_hubs, hub_len, row_len, seed):
-    """A (M x K): rows 0..n_hubs-1 with hub_len entries, the others 3; B (K x N)
-    with row_len entries per row over all N columns: hub rows of hub_len *
-    row_len products."""
-    rng = np.random.default_rng(seed)
-    ra = [np.full(hub_len, i) for i in range(n_hubs)] + [np.repeat(np.arange(n_hubs, M), 3)]
-    ca = [rng.choice(K, size=hub_len, replace=False) for _ in range(n_hubs)] + \
-         [rng.integers(0, K, size=3 * (M - n_hubs))]
-    A = W.from_coo(M, K, np.concatenate(ra), np.concatenate(ca))
-    rb = np.repeat(np.arange(K), row_len)
-    cb = rng.integers(0, N, size=K * row_len)
-    return A, W.from_coo(K, N, rb, cb)
-
-
 @pytest.mark.parametrize("n_hubs", [3, 12])
 def test_split_rows_match_the_oracle(n_hubs):
     # hub rows of about 2500 * 600 = 1.5 M products (> 2^20): split; with 12 of
     # them the 8 split slots run out and some are counted whole
-    A, B = _wide_hubs(300, 3000, 1 << 20, n_hubs, 2500, 600, seed=31 + n_hubs)
+    A, B = wide_hubs(300, 3000, 1 << 20, n_hubs, 2500, 600, seed=31 + n_hubs)
     for seed, T in ((0, TWO32), (1, int(0.5 * TWO32))):
         g = gpu_predict(A, B, sp.SAMPLE_BERNOULLI, seed, T)
         o = oracle_predict(A, B, oracle.BERNOULLI, seed, T)
@@ -106,7 +92,7 @@ def test_split_rows_match_the_oracle(n_hubs):
 
 
 def test_split_rows_with_several_column_passes_and_reference_design():
-    A, B = _wide_hubs(200, 2800, (1 << 21) + 37, 2, 2600, 500, seed=41)  # 1.3 M products, 3 column passes
+    A, B = wide_hubs(200, 2800, (1 << 21) + 37, 2, 2600, 500, seed=41)  # 1.3 M products, 3 column passes
     for ref in (False, True):
         g = gpu_predict(A, B, sp.SAMPLE_BERNOULLI, 5, TWO32, reference=ref)
         o = oracle_predict(A, B, oracle.BERNOULLI, 5, TWO32, reference=ref)
@@ -114,7 +100,7 @@ def test_split_rows_with_several_column_passes_and_reference_design():
 
 
 def test_split_rows_repeated_calls_reuse_the_workspace():
-    A, B = _wide_hubs(300, 3000, 1 << 20, 5, 2400, 550, seed=51)
+    A, B = wide_hubs(300, 3000, 1 << 20, 5, 2400, 550, seed=51)
     dA, dB = sp.DeviceCSR.from_host(A), sp.DeviceCSR.from_host(B)
     ws = sp.Workspace.for_operands(dA, dB)
     o = oracle_predict(A, B, oracle.BERNOULLI, 6, TWO32)
