@@ -610,7 +610,9 @@ int numeric_check(const spgemm_csr_t* A, const float* a_val, const spgemm_csr_t*
   if (c_capacity < 0 || (c_capacity > 0 && (!c_col || !c_val))) return SPGEMM_ERR_INVALID_ARG;
   if (A->cols != B->rows) return SPGEMM_ERR_DIM_MISMATCH;
   if (!csr_fits(A) || !csr_fits(B)) return SPGEMM_ERR_TOO_LARGE;
-  if (ws_bytes < ws_bytes_for(A->rows, A->cols)) return SPGEMM_ERR_WORKSPACE;
+  // the documented size (as for every other call), although only the part for
+  // A's rows and columns is used here
+  if (ws_bytes < ws_bytes_for(A->rows, A->cols, B->cols)) return SPGEMM_ERR_WORKSPACE;
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return SPGEMM_ERR_WORKSPACE;
   return SPGEMM_OK;
 }

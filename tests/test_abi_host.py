@@ -185,6 +185,48 @@ def test_batch_host_errors(lib):
     assert lib.spgemm_predict_batch(None, ws.ptr(), need, None) == sp.ERR_INVALID_ARG
 
 
+def _call_numeric(lib, A, B, ws_bytes, compact=False, a_val=0x6000, b_val=0x7000, alloc=0x8000, c_col=0x9000,
+                  c_val=0xA000, cap=1000, row_start=0xB000, nnz_row=0xC000, res=0xD000, ws=0x10000,
+                  out_rpt=0xE000, out_col=0xF000, out_val=0xF800, out_cap=1000):
+    a, b = A.struct(), B.struct()
+    if compact:
+        return lib.spgemm_numeric_compact(ctypes.byref(a), a_val, ctypes.byref(b), b_val, c_col, c_val, cap,
+                                          row_start, nnz_row, out_rpt, out_col, out_val, out_cap, res, ws,
+                                          ws_bytes, None)
+    return lib.spgemm_numeric_into(ctypes.byref(a), a_val, ctypes.byref(b), b_val, alloc, c_col, c_val, cap,
+                                   row_start, nnz_row, res, ws, ws_bytes, None)
+
+
+@pytest.mark.parametrize("compact", [False, True])
+def test_numeric_host_errors(lib, compact):
+    # every argument the numeric calls check on the host, one at a time; the
+    # good call itself is never made (it would touch the device)
+    A, B = _Fake(100, 50, 300), _Fake(50, 70, 200)
+    a, b = A.struct(), B.struct()
+    ws = lib.spgemm_workspace_size(ctypes.byref(a), ctypes.byref(b))
+
+    def call(**kw):
+        return _call_numeric(lib, kw.pop("A", A), kw.pop("B", B), kw.pop("ws_bytes", ws), compact, **kw)
+
+    assert call(B=_Fake(51, 70, 200)) == sp.ERR_DIM_MISMATCH
+    assert call(A=_Fake(1 << 31, 50, 0), ws_bytes=1 << 40) == sp.ERR_TOO_LARGE
+    assert call(A=_Fake(-1, 50, 0)) == sp.ERR_INVALID_ARG
+    for arg in ("res", "ws", "a_val", "b_val", "row_start", "nnz_row", "c_col", "c_val"):
+        assert call(**{arg: None}) == sp.ERR_INVALID_ARG, arg
+    assert call(cap=-1) == sp.ERR_INVALID_ARG
+    # no values are needed for operands without nonzeros, and no C arrays for
+    # a zero capacity; the other checks still apply
+    assert call(A=_Fake(100, 50, 0), a_val=None, cap=0, c_col=None, c_val=None, ws_bytes=ws - 1) \
+        == sp.ERR_WORKSPACE
+    assert call(ws_bytes=ws - 1) == sp.ERR_WORKSPACE
+    assert call(ws=0x10010) == sp.ERR_WORKSPACE  # misaligned
+    if compact:
+        assert call(out_rpt=None) == sp.ERR_INVALID_ARG
+        assert call(out_cap=-1) == sp.ERR_INVALID_ARG
+        assert call(out_col=None) == sp.ERR_INVALID_ARG
+        assert call(out_val=None) == sp.ERR_INVALID_ARG
+
+
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(sp, "_lib", None)
     monkeypatch.setattr(sp, "library_path", lambda: str(tmp_path / "missing.so"))
