@@ -28,6 +28,15 @@ MUTANTS = {
     "reference drops M": ("(u128)(uint64_t)z * (u128)(uint64_t)M;", "(u128)(uint64_t)z;"),
     "reference drops |S|": ("(u128)(uint64_t)F * (u128)(uint64_t)n_ids;", "(u128)(uint64_t)F;"),
     "sample comparison flipped": ("orc_h32(seed, (uint64_t)i) < threshold", "orc_h32(seed, (uint64_t)i) > threshold"),
+    "sample comparison inclusive": ("orc_h32(seed, (uint64_t)i) < threshold", "orc_h32(seed, (uint64_t)i) <= threshold"),
+    "prediction divides before multiplying": (
+        "p = (int64_t)ceil_div_u128((u128)(uint64_t)flop[i] * (u128)(uint64_t)z, (u128)(uint64_t)f);",
+        "p = (int64_t)((u128)(uint64_t)flop[i] * ceil_div_u128((u128)(uint64_t)z, (u128)(uint64_t)f));"),
+    "prediction swaps z* and f*": (
+        "p = (int64_t)ceil_div_u128((u128)(uint64_t)flop[i] * (u128)(uint64_t)z, (u128)(uint64_t)f);",
+        "p = (int64_t)ceil_div_u128((u128)(uint64_t)flop[i] * (u128)(uint64_t)f, (u128)(uint64_t)z);"),
+    "offsets start at one": ("  offsets[0] = 0;\n  for (int64_t i = 0; i < M; ++i) {\n    int64_t p;\n    if (f == 0)",
+                             "  offsets[0] = 1;\n  for (int64_t i = 0; i < M; ++i) {\n    int64_t p;\n    if (f == 0)"),
     "hash constant typo": ("0xbf58476d1ce4e5b9ull", "0xbf58476d1ce4e5b8ull"),
     "draw scales by M/2": ("* (uint64_t)M) >> 32", "* (uint64_t)M) >> 33"),
     "sample_num rounds up": ("int64_t s = (3 * M) / 1000;", "int64_t s = (3 * M + 999) / 1000;"),
@@ -49,6 +58,7 @@ def _pins():
     yield lambda: P.test_splitmix64_known_answers(g)
     yield P.test_bernoulli_threshold_extremes
     yield P.test_bernoulli_membership_matches_hash
+    yield P.test_bernoulli_threshold_is_strict
     yield lambda: P.test_paper_sample_num(g)
     yield P.test_paper_draw_rows_in_range
     yield lambda: P.test_flop_and_nnz_against_dense_product((17, 33, 9), 0.3)

@@ -55,6 +55,18 @@ def test_bernoulli_membership_matches_hash():
         assert (i in ids) == (oracle.h32(42, i) < T)
 
 
+def test_bernoulli_threshold_is_strict():
+    # Sampling probability T / 2^32 for a uniform 32-bit hash means the rule is
+    # h < T: raising T by one adds exactly the rows whose hash equals T, so a
+    # row whose hash is the threshold itself is not yet sampled.
+    M, seed = 4000, 9
+    for i0 in (0, 17, 2500, M - 1):
+        T = oracle.h32(seed, i0)
+        lo = set(oracle.sample(M, oracle.BERNOULLI, seed, T).tolist())
+        hi = set(oracle.sample(M, oracle.BERNOULLI, seed, T + 1).tolist())
+        assert i0 not in lo and i0 in hi and lo <= hi
+        assert hi - lo == {i for i in range(M) if oracle.h32(seed, i) == T}
+
 def test_paper_sample_num(golden):
     for M, s in golden("paper_sample_num.txt"):
         assert oracle.paper_sample_num(int(M)) == int(s)
