@@ -42,6 +42,8 @@ MUTANTS = {
     "sample_num rounds up": ("int64_t s = (3 * M) / 1000;", "int64_t s = (3 * M + 999) / 1000;"),
     "scan subtracts": ("(u128)(uint64_t)f);\n    pred[i] = p;\n    offsets[i + 1] = offsets[i] + p;",
                        "(u128)(uint64_t)f);\n    pred[i] = p;\n    offsets[i + 1] = offsets[i] - p;"),
+    "symbolic offsets stop a row early": ("for (int64_t i = 0; i < M; ++i) offsets[i + 1] = offsets[i] + nnz[i];",
+                                          "for (int64_t i = 0; i + 1 < M; ++i) offsets[i + 1] = offsets[i] + nnz[i];"),
     "empty sample not flagged": ("if (f == 0) status |= ORC_WARN_EMPTY_SAMPLE;", ""),
     "numeric overwrites the sum": ("            acc[c] += prod;", "            acc[c] = prod;"),
     "numeric squares A's value": ("const double prod = a * (double)b_val[t];", "const double prod = a * a;"),
