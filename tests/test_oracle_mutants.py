@@ -55,25 +55,37 @@ MUTANTS = {
 }
 
 
-def _pins():
+def _independent_pins():
+    """Pins that tie the oracle to something other than its own formulas: known
+    answers, brute force, closed forms, distributions and printed values."""
     g = read_golden
     yield lambda: P.test_splitmix64_known_answers(g)
     yield P.test_bernoulli_threshold_extremes
     yield P.test_bernoulli_membership_matches_hash
     yield P.test_bernoulli_threshold_is_strict
     yield lambda: P.test_paper_sample_num(g)
-    yield P.test_paper_draw_rows_in_range
+    yield P.test_paper_draw_mapping_covers_rows_in_order
     yield lambda: P.test_flop_and_nnz_against_dense_product((17, 33, 9), 0.3)
     yield lambda: P.test_laplacian_2d_closed_form(9)
     yield P.test_periodic_laplacian_uniform_rows
-    for name in ("lap64", "er", "rmat", "rect"):
-        yield lambda n=name: P.test_prediction_invariants(n, oracle.BERNOULLI)
-        yield lambda n=name: P.test_prediction_invariants(n, oracle.PAPER_DRAW)
+    yield lambda: P.test_dense_blocks(7)
+    yield P.test_reference_design_uniform_rows
+    yield P.test_rounding_up_worked_example
     yield lambda: P.test_numeric_against_dense_product((17, 33, 9), 0.5)
     yield lambda: P.test_numeric_laplacian_squared_closed_form(8)
     yield P.test_numeric_sum_identity
     yield P.test_empty_sample_falls_back_to_flop
     yield P.test_paper_draw_counts_repeats
+
+
+def _pins():
+    """Every pin: the independent ones, then the invariant checks that restate
+    the ceiling and the draw formula row by row."""
+    yield from _independent_pins()
+    yield P.test_paper_draw_rows_in_range
+    for name in ("lap64", "er", "rmat", "rect"):
+        yield lambda n=name: P.test_prediction_invariants(n, oracle.BERNOULLI)
+        yield lambda n=name: P.test_prediction_invariants(n, oracle.PAPER_DRAW)
 
 
 @pytest.fixture(scope="module")
@@ -83,28 +95,44 @@ def tmpdir_mod():
     shutil.rmtree(d, ignore_errors=True)
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_reject_mutant(name, tmpdir_mod):
+def _mutant_library(name, tmpdir):
     old, new = MUTANTS[name]
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation anchor for {name!r} not unique"
-    path_c = os.path.join(tmpdir_mod, f"m{abs(hash(name))}.c")
+    path_c = os.path.join(tmpdir, f"m{abs(hash(name))}.c")
     path_so = path_c[:-2] + ".so"
-    with open(path_c, "w") as f:
-        f.write(src.replace(old, new))
-    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", path_c, "-o", path_so], check=True)
+    if not os.path.exists(path_so):
+        with open(path_c, "w") as f:
+            f.write(src.replace(old, new))
+        subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", path_c, "-o", path_so], check=True)
+    return path_so
+
+
+def _rejected_by(pins, path_so):
     prev = oracle.use_library(path_so)
-    caught = False
     try:
-        for pin in _pins():
+        for pin in pins:
             try:
                 pin()
             except AssertionError:
-                caught = True
-                break
+                return True
     finally:
         oracle.restore_library(prev)
-    assert caught, f"no pin rejects the mutant {name!r}"
+    return False
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(name, tmpdir_mod):
+    assert _rejected_by(_pins(), _mutant_library(name, tmpdir_mod)), f"no pin rejects the mutant {name!r}"
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_independent_pins_alone_reject_mutant(name, tmpdir_mod):
+    # Without the checks that restate a formula of the oracle (the ceiling and
+    # the draw mapping recomputed row by row), each mutant must still fail a pin
+    # tied to something else: a closed form, a distribution, a worked example.
+    assert _rejected_by(_independent_pins(), _mutant_library(name, tmpdir_mod)), \
+        f"only a restating check rejects the mutant {name!r}"
 
 
 def test_unmutated_oracle_passes_the_same_pins():

@@ -83,6 +83,26 @@ def test_paper_draw_rows_in_range():
             assert ids[r] == (oracle.h32(5, r) * M) >> 32
 
 
+
+def test_paper_draw_mapping_covers_rows_in_order():
+    # Algorithm 2 scales a uniform number in [0, 1) by M (rid = M * rand): the
+    # row id is monotone in the draw's hash, reaches the whole range [0, M) and
+    # is uniform over it.  A mapping onto part of the rows (M/2, say) misses the
+    # top of the range; one that wraps (h mod M) breaks the order.
+    M, n = 1 << 20, 4000
+    for seed in range(5):
+        ids = oracle.sample(M, oracle.PAPER_DRAW, seed, sample_num=n).astype(np.int64)
+        assert len(ids) == n and ids.min() >= 0 and ids.max() < M
+        assert ids.max() > 0.99 * M and ids.min() < 0.01 * M
+        sd = M / math.sqrt(12 * n)  # standard deviation of the mean of n uniform draws
+        assert abs(ids.mean() - (M - 1) / 2) < 6 * sd
+        # 16 equal bins: counts within 6 sigma of n/16 each
+        cnt = np.bincount(ids * 16 // M, minlength=16)
+        assert np.all(np.abs(cnt - n / 16) < 6 * math.sqrt(n / 16))
+        h = np.array([oracle.h32(seed, r) for r in range(n)], dtype=np.int64)
+        order = np.argsort(h, kind="stable")
+        assert np.all(np.diff(ids[order]) >= 0)
+
 # ---------------------------------------------------------------- brute force
 @pytest.mark.parametrize("shape", [(1, 1, 1), (5, 3, 7), (17, 33, 9), (40, 64, 64), (64, 20, 50)])
 @pytest.mark.parametrize("density", [0.05, 0.3, 0.9])
@@ -177,6 +197,8 @@ def test_periodic_laplacian_uniform_rows():
         for seed in (0, 1, 2):
             r = oracle.predict(A, A, oracle.BERNOULLI, seed, int(0.2 * TWO32))
             assert r["status"] == 0 and np.all(r["pred"] == 13)
+            # the allocation offsets of rows of 13: 0, 13, 26, ...
+            assert np.array_equal(r["offsets"], 13 * np.arange(A.rows + 1))
 
 
 @pytest.mark.parametrize("dims", [(3, 3, 3), (4, 5, 6), (8, 8, 8), (16, 4, 9)])
@@ -203,6 +225,51 @@ def test_dense_blocks(b):
     r = oracle.predict(A, A, oracle.BERNOULLI, 3, int(0.3 * TWO32))
     assert np.all(r["pred"] == b) and Fraction(r["flop_s"], r["nnz_s"]) == b
 
+
+
+def test_reference_design_uniform_rows():
+    # Eq. 2 on a matrix whose output rows all have the same FLOP f and nnz z:
+    # any non-empty sample gives z* = z |S| and F = f M, so Z1* = z* M / |S| =
+    # z M = Z exactly, and every row's prediction flop_i / CR1 = f z M / F is z.
+    # Torus 5-point stencil: f = 25, z = 13; dense b x b blocks: f = b^2, z = b.
+    cases = [(W.laplacian_2d(N, periodic=True), 13) for N in (5, 8, 33)]
+    cases += [(W.dense_blocks(64 * b, b), b) for b in (2, 7, 32)]
+    for A, z in cases:
+        M = A.rows
+        runs = [(oracle.BERNOULLI, seed, int(ratio * TWO32), 0)
+                for seed in range(3) for ratio in (0.2, 0.5)]
+        runs += [(oracle.PAPER_DRAW, seed, 0, s) for seed in range(3) for s in (7, min(40, M))]
+        for mode, seed, T, s in runs:
+            r = oracle.predict_reference(A, A, mode, seed, T, s)
+            if r["n_sampled"] < 2:
+                continue
+            assert r["status"] == 0, (mode, seed)
+            assert np.all(r["pred"] == z), (mode, seed, np.unique(r["pred"]))
+            assert r["pred_total"] == z * M and r["offsets"][-1] == z * M
+            e = oracle.estimates(r["flop_total"], z * M, r["flop_s"], r["nnz_s"], M, r["n_sampled"])
+            assert e["Z1"] == z * M and e["eps1"] == 0
+
+
+def test_rounding_up_worked_example():
+    # Hand-worked case for the rounding of flop_i / r*: three dense 2 x 2 blocks
+    # and two dense 3 x 3 blocks (12 rows).  Six rows have flop 4 and nnz 2, six
+    # have flop 9 and nnz 3, so with every row sampled z* = 30 and f* = 78, and
+    # r* = 78 / 30 = 2.6.  A row of flop 4 predicts 4 / 2.6 = 1.54 -> 2 and a row
+    # of flop 9 predicts 9 / 2.6 = 3.46 -> 4 (rounded up; down would give 1 and 3).
+    # The reference design (p = 1, F = f*) gives the same.
+    rows, cols = [], []
+    starts = [(0, 2), (2, 2), (4, 2), (6, 3), (9, 3)]
+    for s0, b in starts:
+        for i in range(b):
+            for j in range(b):
+                rows.append(s0 + i)
+                cols.append(s0 + j)
+    A = W.from_coo(12, 12, np.array(rows), np.array(cols))
+    want = [2] * 6 + [4] * 6
+    for fn in (oracle.predict, oracle.predict_reference):
+        r = fn(A, A, oracle.BERNOULLI, 0, TWO32)
+        assert (r["flop_s"], r["nnz_s"], r["n_sampled"]) == (78, 30, 12)
+        assert r["pred"].tolist() == want and r["pred_total"] == 36
 
 # ---------------------------------------------------------------- the method
 def _cases():
