@@ -183,6 +183,20 @@ int spgemm_validate_csr(const spgemm_csr_t* A, spgemm_result_t* res, void* ws, s
  * benchmarks, not for concurrent use from several threads.  Returns SPGEMM_OK. */
 int spgemm_set_profile_events(void* before, void* after);
 
+/* Roofline calibration (a library utility; the paper has no counterpart).  The
+ * FLOP pass of Algorithm 1 reads A's column ids in order and, for each, one
+ * byte of a table of B's row lengths at a scattered position; on this GPU the
+ * rate of those scattered lookups, not HBM bandwidth, bounds it.  This call
+ * runs that access pattern alone: it streams col[0..n) (int32, device memory,
+ * 16-byte aligned) and reads table[col[j]] (uint8, device memory, table_bytes
+ * long; ids outside [0, table_bytes) count as zero) for every j, and writes
+ * the sum of the bytes read to *out (uint64, device memory) on `stream`.
+ * Timed by the caller, n / time is the device's lookup ceiling for that id
+ * stream.  Returns SPGEMM_ERR_INVALID_ARG for a negative size, a null pointer
+ * or an unaligned col, before anything is queued. */
+int spgemm_lookup_probe(const int32_t* col, int64_t n, const uint8_t* table, int64_t table_bytes,
+                        uint64_t* out, void* stream);
+
 /* spgemm_predict_structure without a caller-supplied workspace.  The paper has
  * no counterpart: this is a library utility for callers that cannot allocate
  * device memory themselves, for example a host program whose device memory is
@@ -193,8 +207,10 @@ int spgemm_set_profile_events(void* before, void* after);
  * The scratch space is a fixed array of device memory compiled into the library,
  * sized for A.rows, A.cols and B.cols <= SPGEMM_STATIC_MAX_ROWS (about 35 MB).
  * Every GPU that loads the library holds it until the process exits.  Larger
- * problems are rejected with SPGEMM_ERR_STATIC_CAPACITY before anything is
- * queued.  The call allocates
+ * problems are rejected with SPGEMM_ERR_STATIC_CAPACITY.  Every host check
+ * (the arguments and codes of spgemm_predict_structure, then the capacity)
+ * runs before anything is queued, so a call that returns a negative code has
+ * queued no work.  The call allocates
  * nothing (no cudaMalloc/cudaFree, no allocating library routine): the caller
  * still passes the inputs, outputs and result record, as for
  * spgemm_predict_structure, and gets the same results.

@@ -118,6 +118,8 @@ def load():
     lib.spgemm_predict_structure_static.restype = ctypes.c_int
     lib.spgemm_set_profile_events.argtypes = [P, P]
     lib.spgemm_set_profile_events.restype = ctypes.c_int
+    lib.spgemm_lookup_probe.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, P, P]
+    lib.spgemm_lookup_probe.restype = ctypes.c_int
     I = ctypes.POINTER(BatchItemStruct)
     T = ctypes.POINTER(TuningStruct)
     PL = ctypes.POINTER(PlanStruct)
@@ -314,6 +316,13 @@ def spgemm_set_profile_events(before, after):
     b = None if before is None else ctypes.c_void_p(before.cuda_event)
     a = None if after is None else ctypes.c_void_p(after.cuda_event)
     return load().spgemm_set_profile_events(b, a)
+
+
+def spgemm_lookup_probe(col, table, out, stream=None):
+    """Stream col (int32) with one lookup into table (uint8) per id; the sum of the
+    bytes read goes to out (int64/uint64 tensor of one element)."""
+    return load().spgemm_lookup_probe(_ptr(col), int(col.numel()), _ptr(table), int(table.numel()), _ptr(out),
+                                      _stream(stream))
 
 
 def _numel(t):

@@ -13,6 +13,7 @@
 #include "k_dedup.cuh"
 #include "k_flop.cuh"
 #include "k_predict.cuh"
+#include "k_probe.cuh"
 #include "k_scan.cuh"
 
 using namespace spg;
@@ -321,11 +322,9 @@ int predict_common(const spgemm_csr_t* A, const spgemm_csr_t* B, const spgemm_co
 // object: its device address comes from cudaGetSymbolAddress, looked up once per
 // device below and passed to the kernels.
 constexpr size_t kStaticHeaderBytes = sizeof(WsHeader) + sizeof(Slot) * kMaxSlots;
-constexpr size_t kStaticRowBytes = ((size_t)SPGEMM_STATIC_MAX_ROWS * 4 + 255) / 256 * 256;
-constexpr size_t kStaticDegBytes = ((size_t)SPGEMM_STATIC_MAX_ROWS + 16 + 255) / 256 * 256;
-constexpr size_t kStaticHugeBytes =
-    sizeof(HugeSlot) * kHugeSlots + (size_t)kHugeSlots * kMaxParts * ((size_t)SPGEMM_STATIC_MAX_ROWS + 2047) / 2048 * 64 * 4;
-constexpr size_t kStaticBytes = kStaticHeaderBytes + 2 * kStaticRowBytes + kStaticDegBytes + kStaticHugeBytes;
+constexpr size_t kStaticBytes = ws_bytes_for(SPGEMM_STATIC_MAX_ROWS, SPGEMM_STATIC_MAX_ROWS, SPGEMM_STATIC_MAX_ROWS);
+static_assert(kStaticBytes >= kStaticHeaderBytes + 2 * (size_t)SPGEMM_STATIC_MAX_ROWS * 4 + (size_t)SPGEMM_STATIC_MAX_ROWS,
+              "the scratch holds the header, the row queue, the FLOP buffer and the byte table");
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 void* g_static_ptr[kMaxDevices];
@@ -336,6 +335,7 @@ void init_static_scratch(int dev) {
   void* p = nullptr;
   g_static_err[dev] = cudaGetSymbolAddress(&p, g_static_scratch);
   g_static_ptr[dev] = g_static_err[dev] == cudaSuccess ? p : nullptr;
+  if (g_static_err[dev] != cudaSuccess) cudaGetLastError();
 }
 
 // ---- batched prediction ---------------------------------------------------------
@@ -814,24 +814,38 @@ int spgemm_predict_structure_static(const spgemm_csr_t* A, const spgemm_csr_t* B
                                     const spgemm_config_t* cfg, int32_t* pred_row,
                                     int64_t* offsets, int32_t* flop_row, spgemm_result_t* res,
                                     void* stream) {
-  if (!csr_ok(A)) return SPGEMM_ERR_INVALID_ARG;
-  if (A->rows > SPGEMM_STATIC_MAX_ROWS || A->cols > SPGEMM_STATIC_MAX_ROWS) return SPGEMM_ERR_STATIC_CAPACITY;
+  // Every host check comes first, so that a rejected call has queued nothing.
+  if (!csr_ok(A) || !csr_ok(B) || !res) return SPGEMM_ERR_INVALID_ARG;
+  if (A->cols != B->rows) return SPGEMM_ERR_DIM_MISMATCH;
+  if (!csr_fits(A) || !csr_fits(B)) return SPGEMM_ERR_TOO_LARGE;
+  if (!offsets || (!pred_row && A->rows > 0)) return SPGEMM_ERR_INVALID_ARG;
+  long long n_cand = 0;
+  int rc = sample_candidates(cfg, A->rows, &n_cand);
+  if (rc) return rc;
+  if (A->rows > SPGEMM_STATIC_MAX_ROWS || A->cols > SPGEMM_STATIC_MAX_ROWS || B->cols > SPGEMM_STATIC_MAX_ROWS)
+    return SPGEMM_ERR_STATIC_CAPACITY;
+  if (ws_bytes_for(A->rows, A->cols, B->cols) > kStaticBytes) return SPGEMM_ERR_STATIC_CAPACITY;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SPGEMM_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return SPGEMM_ERR_CUDA;
+  }
   std::call_once(g_static_once[dev], init_static_scratch, dev);
   void* ws = g_static_ptr[dev];
   if (!ws) return SPGEMM_ERR_CUDA;
-  if (!csr_ok(B) || B->cols > SPGEMM_STATIC_MAX_ROWS) return B && csr_ok(B) ? SPGEMM_ERR_STATIC_CAPACITY : SPGEMM_ERR_INVALID_ARG;
-  if (ws_bytes_for(A->rows, A->cols, B->cols) > kStaticBytes) return SPGEMM_ERR_STATIC_CAPACITY;
+  if (!limits()) return SPGEMM_ERR_CUDA;
   // Header, per-block slots and flag epoch, the heavy-row queue and the
-  // split-row slots start from zero on every call (a call that ended with an
-  // error may have left them dirty).
+  // split-row slots (present when B has columns) start from zero on every call
+  // (a call that ended with an error may have left them dirty).
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Workspace w = ws_carve(ws, A->rows, A->cols, B->cols);
-  if (cudaMemsetAsync(ws, 0, kStaticHeaderBytes, st) != cudaSuccess ||
-      cudaMemsetAsync(w.heavy, 0, (size_t)(A->rows > 0 ? A->rows : 1) * sizeof(int), st) != cudaSuccess ||
-      cudaMemsetAsync(w.huge, 0, sizeof(HugeSlot) * kHugeSlots, st) != cudaSuccess)
+  bool ok = cudaMemsetAsync(ws, 0, kStaticHeaderBytes, st) == cudaSuccess &&
+            cudaMemsetAsync(w.heavy, 0, (size_t)(A->rows > 0 ? A->rows : 1) * sizeof(int), st) == cudaSuccess;
+  if (ok && w.huge) ok = cudaMemsetAsync(w.huge, 0, sizeof(HugeSlot) * kHugeSlots, st) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();  // leave no error behind for the next call to find
     return SPGEMM_ERR_CUDA;
+  }
   return predict_common(A, B, cfg, pred_row, offsets, flop_row, res, ws, kStaticBytes, stream, false);
 }
 
@@ -949,6 +963,23 @@ int spgemm_batch_autotune(const spgemm_batch_item_t* items, int32_t n, void* ws,
   *best = pick;
   if (best_ms) *best_ms = total;
   return SPGEMM_OK;
+}
+
+int spgemm_lookup_probe(const int32_t* col, int64_t n, const uint8_t* table, int64_t table_bytes,
+                        uint64_t* out, void* stream) {
+  if (n < 0 || table_bytes < 0 || !out) return SPGEMM_ERR_INVALID_ARG;
+  if (n > 0 && (!col || (reinterpret_cast<uintptr_t>(col) & 15) != 0)) return SPGEMM_ERR_INVALID_ARG;
+  if (table_bytes > 0 && !table) return SPGEMM_ERR_INVALID_ARG;
+  const DeviceLimits* L = limits();
+  if (!L) return SPGEMM_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(out, 0, sizeof(uint64_t), st) != cudaSuccess) {
+    cudaGetLastError();
+    return SPGEMM_ERR_CUDA;
+  }
+  k_lookup_probe<<<L->sms, kProbeThreads, 0, st>>>(col, n, table, table_bytes,
+                                                   reinterpret_cast<unsigned long long*>(out));
+  return cudaGetLastError() == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 
 int spgemm_set_profile_events(void* before, void* after) {

@@ -84,12 +84,12 @@ struct Workspace {
 // B row lengths of at least kDegEscape are read from B.rpt instead of the table.
 constexpr int kDegEscape = 255;
 
-inline size_t ws_round(size_t b) { return ((b + 255) / 256) * 256; }
-inline long long ws_huge_words(int64_t N) { return N > 0 ? (N + 2047) / 2048 * 64 : 0; }
+constexpr size_t ws_round(size_t b) { return ((b + 255) / 256) * 256; }
+constexpr long long ws_huge_words(int64_t N) { return N > 0 ? (N + 2047) / 2048 * 64 : 0; }
 
 // Bytes for M rows of A, K columns of A (= rows of B) and N columns of B (the
 // split-row bitmaps; N = 0 leaves them out).
-inline size_t ws_bytes_for(int64_t M, int64_t K, int64_t N = 0) {
+constexpr size_t ws_bytes_for(int64_t M, int64_t K, int64_t N = 0) {
   const size_t m = (size_t)(M > 0 ? M : 1), k = (size_t)(K > 0 ? K : 1);
   size_t b = sizeof(WsHeader) + sizeof(Slot) * kMaxSlots + 2 * ws_round(m * 4) + ws_round(k + 16);
   if (N > 0) b += sizeof(HugeSlot) * kHugeSlots + (size_t)kHugeSlots * kMaxParts * (size_t)ws_huge_words(N) * 4;

@@ -491,7 +491,11 @@ __device__ __noinline__ bool heavy_phase(const PredArgs& p, PredStatic& ss, unsi
   bool flop_in_smem = true;
   unsigned* tab = reinterpret_cast<unsigned*>(pdyn);
   HugeSlot* hs = a.ws.huge;
-  const uint64_t t_start = global_ns();
+  // the wait for other blocks' heavy rows gives up after about a second
+  // without progress (a large input may legitimately keep the blocks busy
+  // for longer than that in total)
+  uint64_t t_start = global_ns();
+  unsigned seen_done = 0;
   for (;;) {
     if (t == 0) {
       ss.s_part = hs ? claim_part(hs) : -1;
@@ -587,8 +591,13 @@ __device__ __noinline__ bool heavy_phase(const PredArgs& p, PredStatic& ss, unsi
       if (t == 0) {
         const unsigned nh = (unsigned)min((unsigned long long)flag_load(&hdr->heavy_count),
                                           (unsigned long long)d.heavy_cap);
-        ss.s_last = flag_load(&hdr->heavy_done) >= nh;
+        const unsigned hd = flag_load(&hdr->heavy_done);
+        ss.s_last = hd >= nh;
         if (!ss.s_last) {
+          if (hd != seen_done) {  // progress: the limit restarts
+            seen_done = hd;
+            t_start = global_ns();
+          }
           __nanosleep(128);
           if (global_ns() - t_start > 1000000000ull) {
             atomicOr(&hdr->status, (unsigned)SPGEMM_STATUS_ERR_TIMEOUT);

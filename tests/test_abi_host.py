@@ -232,3 +232,41 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(sp, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         sp.load()
+
+
+def _call_static(lib, A, B, cfg, pred=0x4000, offs=0x5000, res=0x3000):
+    a, b = A.struct(), B.struct()
+    return lib.spgemm_predict_structure_static(ctypes.byref(a), ctypes.byref(b),
+                                               ctypes.byref(cfg) if cfg is not None else None,
+                                               pred, offs, None, res, None)
+
+
+def test_static_entry_point_host_errors(lib):
+    # The entry point without a workspace checks everything on the host before
+    # it touches the device: a rejected call returns its code with nothing queued
+    # (these calls never reach a CUDA call, so they run without a GPU).
+    A, B = _Fake(100, 50, 300), _Fake(50, 70, 200)
+    cfg = sp.config(ratio=0.01)
+    assert _call_static(lib, A, _Fake(51, 70, 200), cfg) == sp.ERR_DIM_MISMATCH
+    assert _call_static(lib, A, B, cfg, res=0) == sp.ERR_INVALID_ARG
+    assert _call_static(lib, A, B, cfg, pred=0) == sp.ERR_INVALID_ARG
+    assert _call_static(lib, A, B, cfg, offs=0) == sp.ERR_INVALID_ARG
+    assert _call_static(lib, A, B, None) == sp.ERR_INVALID_ARG
+    assert _call_static(lib, _Fake(-1, 50, 0), B, cfg) == sp.ERR_INVALID_ARG
+    assert _call_static(lib, A, B, sp.config(threshold=(1 << 32) + 1)) == sp.ERR_INVALID_ARG
+    assert _call_static(lib, A, B, sp.config(mode=7, ratio=0.1)) == sp.ERR_INVALID_ARG
+    assert _call_static(lib, A, B, sp.config(mode=sp.SAMPLE_PAPER_DRAW, sample_num=101)) == sp.ERR_INVALID_ARG
+    assert _call_static(lib, _Fake(1 << 31, 50, 0), B, cfg) == sp.ERR_TOO_LARGE
+    big = sp.STATIC_MAX_ROWS + 1
+    # any one of A.rows, A.cols, B.cols above the limit
+    assert _call_static(lib, _Fake(big, 50, 0), B, cfg) == sp.ERR_STATIC_CAPACITY
+    assert _call_static(lib, _Fake(100, big, 0), _Fake(big, 70, 0), cfg) == sp.ERR_STATIC_CAPACITY
+    assert _call_static(lib, A, _Fake(50, big, 0), cfg) == sp.ERR_STATIC_CAPACITY
+
+
+def test_lookup_probe_host_errors(lib):
+    assert lib.spgemm_lookup_probe(0x1000, -1, 0x2000, 10, 0x3000, None) == sp.ERR_INVALID_ARG
+    assert lib.spgemm_lookup_probe(0x1000, 10, 0x2000, 10, None, None) == sp.ERR_INVALID_ARG
+    assert lib.spgemm_lookup_probe(0x1004, 10, 0x2000, 10, 0x3000, None) == sp.ERR_INVALID_ARG  # unaligned ids
+    assert lib.spgemm_lookup_probe(None, 10, 0x2000, 10, 0x3000, None) == sp.ERR_INVALID_ARG
+    assert lib.spgemm_lookup_probe(0x1000, 10, None, 10, 0x3000, None) == sp.ERR_INVALID_ARG
