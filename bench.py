@@ -167,16 +167,17 @@ def kernel_source_hash():
 
 
 def profiled_traffic():
-    """DRAM bytes per launch of k_predict from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_predict_er_n2e20.md")
+    """DRAM bytes per launch of k_predict from the committed ncu summary
+    (profiles/k_predict_er_n2e20.json), if it was taken on the current kernel
+    source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_predict_er_n2e20.json")
     if not os.path.exists(path):
         return None
-    text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+source_hash:\s*([0-9a-f]+)", text)
-    if not m or m.group(2) != kernel_source_hash():
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
         return None
-    return int(m.group(1))
+    return int(d["traffic_bytes_per_launch"])
 
 
 def algorithmic_bytes(A, f_s, n_s):
@@ -190,6 +191,8 @@ def algorithmic_bytes(A, f_s, n_s):
 
 # ------------------------------------------------------------------ CPU oracle baseline
 def cpu_oracle_baseline(A, seconds=12.0):
+    """The oracle on the machine's host cores, all of them and then one (Sec. VI-B
+    protocol for the single core: one warm-up run, the mean of ten)."""
     import oracle
     T = threshold()
     n = 0
@@ -200,54 +203,144 @@ def cpu_oracle_baseline(A, seconds=12.0):
         dt = time.perf_counter() - t0
         if dt >= seconds or n >= 200:
             break
-    return {"value": A.nnz * n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"the full workload, {n} predictions (seeds 0..{n - 1}), {dt:.1f} s"}
-
-
-def row_slice(A, r0, r1):
-    b, e = int(A.rpt[r0]), int(A.rpt[r1])
-    return W.CSR(r1 - r0, A.cols, (A.rpt[r0:r1 + 1] - b).astype(np.int32), A.col[b:e])
+    out = {"value": A.nnz * n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"the full workload, {n} predictions (seeds 0..{n - 1}), {dt:.1f} s"}
+    prev = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        oracle.predict(A, A, oracle.BERNOULLI, 0, T)  # warm-up
+        t1 = time.perf_counter()
+        for k in range(10):
+            oracle.predict(A, A, oracle.BERNOULLI, k, T)
+        d1 = time.perf_counter() - t1
+    finally:
+        oracle.set_num_threads(prev)
+    out["single_core"] = {"value": A.nnz * 10 / d1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                          "sample": f"the full workload, one warm-up then the mean of 10 predictions, {d1:.1f} s"}
+    return out
 
 
 def run_reference(args):
-    """The reference arm: the CPU oracle as it stands, on bounded samples."""
+    """The reference arm: the CPU oracle as it stands, on the machine's host cores,
+    one full prediction of the bench workload per step (same config, metric
+    and unit as the GPU arm)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
     A = make_input(0)
     T = threshold()
-    nslice = 64
-    step = A.rows // nslice
-
-    def one(k):
-        s = (k % nslice) * step
-        S = row_slice(A, s, s + step)
-        t = time.perf_counter()
-        oracle.predict(S, A, oracle.BERNOULLI, k, T)
-        return S.nnz, time.perf_counter() - t
-
     for k in range(args.warmup):
-        one(k)
-    units, secs = 0, 0.0
+        oracle.predict(A, A, oracle.BERNOULLI, k, T)
+    t0 = time.perf_counter()
     for k in range(args.steps):
-        u, dt = one(k)
-        units += u
-        secs += dt
-    value = units / secs
+        oracle.predict(A, A, oracle.BERNOULLI, k, T)
+    secs = time.perf_counter() - t0
+    value = A.nnz * args.steps / secs
     cb = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-          "sample": f"each step: rows of one 1/{nslice} slice of A times the full A (cycling), "
-                    f"{args.steps} steps"}
+          "sample": f"the full workload, one prediction per step (seeds 0..{args.steps - 1}), {secs:.1f} s"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": dict(WORKLOAD), "cpu_baseline": cb,
+            "data": "synthetic", "config": dict(WORKLOAD, nnz=A.nnz), "same_config": True, "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
 # ------------------------------------------------------------------ GPU arm
+CONFIG1 = {"workload": "C=A*A, A 2D 5-point Laplacian on a 64x64 grid (n=4096), int32 CSR, Bernoulli 1% row sample",
+           "gen": "laplacian_2d(64)", "sample_ratio": 0.01}
+CONFIG3 = {"workload": "C=A*A, A R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), duplicates "
+                       "merged, int32 CSR, Bernoulli 0.5% row sample", "gen_seed": 3000, "sample_ratio": 0.005}
+
+
+def measure_config(sp, torch, dev, flush, A, ratio, steps, latency=False):
+    """One config beside the headline: the prediction call timed with CUDA
+    events (L2 flushed before every step), the exact symbolic phase once, the
+    prediction errors, and the HBM fraction of the call (its algorithmic bytes
+    include the 4 f* bytes of sampled B column ids)."""
+    from paper_2207_13848_gb300.report import estimates
+    stream = torch.cuda.current_stream()
+    dA = sp.DeviceCSR.from_host(A, dev)
+    ws = sp.Workspace.for_operands(dA, dA, dev)
+    M = A.rows
+    pred = torch.empty(M, dtype=torch.int32, device=dev)
+    offs = torch.empty(M + 1, dtype=torch.int64, device=dev)
+    res = sp.new_result(dev)
+    cfg = sp.config(threshold=int(ratio * TWO32), seed=0)
+
+    def call():
+        rc = sp.spgemm_predict_structure(dA, dA, cfg, pred, offs, None, res, ws, stream)
+        if rc != sp.OK:
+            raise RuntimeError(sp.spgemm_status_string(rc))
+
+    for _ in range(3):
+        flush.fill_(1)
+        call()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k, (a, b) in enumerate(ev):
+        flush.fill_(k & 0xff)
+        a.record(stream)
+        call()
+        b.record(stream)
+    torch.cuda.synchronize()
+    t = sorted(a.elapsed_time(b) for a, b in ev)
+    r = sp.read_result(res)
+    if r["status"] & (sp.STATUS_ERR_BAD_INPUT | sp.STATUS_ERR_TIMEOUT):
+        raise RuntimeError(f"device status {r['status']}")
+    nnz_row = torch.empty(M, dtype=torch.int32, device=dev)
+    sres = sp.new_result(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(2)
+    e0.record(stream)
+    rc = sp.spgemm_symbolic_exact(dA, dA, nnz_row, offs, sres, ws, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if rc != sp.OK:
+        raise RuntimeError(sp.spgemm_status_string(rc))
+    Z = sp.read_result(sres)["pred_total"]
+    est = estimates(r["flop_total"], Z, r["flop_s"], r["nnz_s"], M, r["n_sampled"])
+    p50 = t[len(t) // 2]
+    bytes_ = algorithmic_bytes(A, r["flop_s"], r["n_sampled"])
+    peak, peak_src = measured_peaks()
+    out = {"steps": steps, "nnz": A.nnz, "n": M, "F": r["flop_total"], "f_s": r["flop_s"], "z_s": r["nnz_s"],
+           "n_sampled": r["n_sampled"], "Z": Z,
+           "call_us": {"p50": 1e3 * p50, "min": 1e3 * t[0], "mean": 1e3 * sum(t) / len(t)},
+           "input_nnz_per_s": A.nnz / (p50 * 1e-3), "sampled_products_per_s": r["flop_s"] / (p50 * 1e-3),
+           "roofline": {"bound": "hbm", "achieved": bytes_ / (p50 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": bytes_ / (p50 * 1e-3) / 1e9 / peak, "algorithmic_bytes": bytes_,
+                        "peak_source": peak_src},
+           "exact_symbolic_us": 1e3 * e0.elapsed_time(e1),
+           "accuracy": {"eps1": est["eps1"], "eps_f": est["eps_f"], "eps2": est["eps2"]},
+           "l2": "flushed before every step (512 MiB write)"}
+    if latency:
+        out["latency_us_p50_of_%d" % steps] = 1e3 * p50
+    return out
+
+
+def lookup_ceiling(sp, torch, dev, flush, dA, reps=20):
+    """The device's rate of scattered one-byte lookups for this A.col stream
+    (spgemm_lookup_probe over a table of A.cols bytes), median of `reps` runs
+    with the L2 flushed before each."""
+    stream = torch.cuda.current_stream()
+    tab = torch.randint(0, 32, (dA.cols,), dtype=torch.uint8, device=dev)
+    out = torch.zeros(1, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        flush.fill_(1)
+        if sp.spgemm_lookup_probe(dA.col, tab, out, stream) != sp.OK:
+            raise RuntimeError("lookup probe failed")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k, (a, b) in enumerate(ev):
+        flush.fill_(k & 0xff)
+        a.record(stream)
+        sp.spgemm_lookup_probe(dA.col, tab, out, stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    t = sorted(a.elapsed_time(b) for a, b in ev)
+    return dA.nnz / (t[len(t) // 2] * 1e-3), t[len(t) // 2]
+
+
 def run_ours(args):
     import torch
 
@@ -438,6 +531,22 @@ def run_ours(args):
                      "n_sampled": r["n_sampled"]},
         "clocks": clk,
     }
+    # the FLOP pass's own ceiling: scattered lookups at the rate the device
+    # sustains for this id stream, measured now on the same input
+    ceil_rate, ceil_ms = lookup_ceiling(sp, torch, dev, flush, dA)
+    rate = A.nnz / (t_kern * 1e-3)
+    line["roofline_lookup"] = {"bound": "l2_lookup_rate", "achieved": rate, "peak": ceil_rate, "unit": "lookups/s",
+                               "frac": rate / ceil_rate, "lookups_per_launch": A.nnz,
+                               "peak_source": "measured in this run: spgemm_lookup_probe (A.col streamed, one "
+                                              "scattered byte lookup per id, nothing else), median of 20, "
+                                              f"{1e3 * ceil_ms:.1f} us"}
+    if not args.skip_configs:
+        cf = {}
+        cf["config1_lap2d_64"] = dict(CONFIG1, **measure_config(sp, torch, dev, flush, W.laplacian_2d(64), 0.01,
+                                                               100, latency=True))
+        cf["config3_rmat_20"] = dict(CONFIG3, **measure_config(sp, torch, dev, flush,
+                                                              W.rmat(20, 16, seed=CONFIG3["gen_seed"]), 0.005, 20))
+        line["configs"] = cf
     if nranks == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_baseline(A, args.cpu_seconds)
     if rank == 0:
@@ -728,6 +837,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-configs", action="store_true",
+                    help="leave out the 2D 5-point (n=4096) and R-MAT scale 20 measurements")
     ap.add_argument("--suite", choices=("predict", "serve", "batch", "accuracy", "numeric"), default="predict",
                     help="predict (default): the headline line; serve / batch: the serving loop "
                          "and the batched predictor")
