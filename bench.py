@@ -555,6 +555,23 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------ other suites
+def _family_job(st, n, v):
+    A, B, name = W.family_case(st, n, v)
+    return st, n, v, A, (None if B is A else B), name
+
+
+def family_cases(sizes, variants=range(25), structures=None, workers=None):
+    """The synthetic family's cases (structure, n, variant, A, B, name), made
+    by worker processes (spawn) in parallel; B is A for the square cases."""
+    import multiprocessing as mp
+    structures = W.STRUCTURES if structures is None else structures
+    jobs = [(st, n, v) for st in structures for n in sizes for v in variants]
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        out = pool.starmap(_family_job, jobs, chunksize=1)
+    return [(st, n, v, A, A if B is None else B, name) for st, n, v, A, B, name in out]
+
+
 def _family_pool(sizes, variants, dev):
     import paper_2207_13848_gb300 as sp
     pool, names = [], []
@@ -605,22 +622,23 @@ def run_serve(args):
 
 def run_batch(args):
     """Batched predictor vs one spgemm_predict_structure launch per case on the
-    family (5 structures x n = 2^12..2^18 x 25 variants), same results."""
+    family (5 structures x n = 2^12..2^20 x 25 variants: 625 cases), same
+    results."""
     import torch
     import paper_2207_13848_gb300 as sp
     from paper_2207_13848_gb300 import build as spbuild
+    T = threshold()
+    exps = tuple(args.batch_sizes)
+    fam = family_cases([1 << e for e in exps])  # before the first CUDA call (spawned workers)
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     spbuild.build()
-    T = threshold()
     cases = []
-    for st in W.STRUCTURES:
-        for e in (12, 14, 16, 18):
-            for v in range(25):
-                A, B, _ = W.family_case(st, 1 << e, v)
-                dA = sp.DeviceCSR.from_host(A, dev)
-                dB = dA if B is A else sp.DeviceCSR.from_host(B, dev)
-                cases.append((dA, dB, sp.config(threshold=T, seed=v)))
+    for st, n, v, A, B, _ in fam:
+        dA = sp.DeviceCSR.from_host(A, dev)
+        dB = dA if B is A else sp.DeviceCSR.from_host(B, dev)
+        cases.append((dA, dB, sp.config(threshold=T, seed=v)))
+    del fam
     stream = torch.cuda.current_stream()
     # per-case launches: one workspace and output set per case, allocated up front
     per = []
@@ -645,19 +663,21 @@ def run_batch(args):
         torch.cuda.synchronize()
         return sorted(a.elapsed_time(b) for a, b in ev)
 
+    steps = max(3, min(args.steps, 20))
     per_case()
-    t_per = timed(per_case, args.steps)
+    t_per = timed(per_case, steps)
     batch = sp.Batch(cases, device=dev)
     best, best_ms = batch.autotune(reps=3)
     batch.run()
-    t_batch = timed(batch.run, args.steps)
+    t_batch = timed(batch.run, steps)
     # same integers: every case's result record and offsets[M]
     torch.cuda.synchronize()
     rb = batch.results()
     same = all(sp.read_result(per[i][6]) == rb[i] for i in range(len(cases)))
     line = {"suite": "batch", "metric": "ms per pass over all cases: batched vs per-case launches",
-            "n_cases": len(cases), "cases": "5 structures x n=2^12..2^18 x 25 variants (2-64 nnz/row, "
-                                            "odd variants rectangular), 1% Bernoulli",
+            "n_cases": len(cases), "steps": steps,
+            "cases": "5 structures x n=" + ",".join(f"2^{e}" for e in exps) + " x 25 variants (2-64 nnz/row, "
+                     "odd variants rectangular), 1% Bernoulli",
             "per_case_ms": {"median": t_per[len(t_per) // 2], "min": t_per[0]},
             "batch_ms": {"median": t_batch[len(t_batch) // 2], "min": t_batch[0]},
             "speedup_median": t_per[len(t_per) // 2] / t_batch[len(t_batch) // 2],
@@ -842,6 +862,8 @@ def main(argv=None):
     ap.add_argument("--suite", choices=("predict", "serve", "batch", "accuracy", "numeric"), default="predict",
                     help="predict (default): the headline line; serve / batch: the serving loop "
                          "and the batched predictor")
+    ap.add_argument("--batch-sizes", type=int, nargs="+", default=[12, 14, 16, 18, 20],
+                    help="log2 of the family's sizes for --suite batch (default: all five, 625 cases)")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-slots", type=int, default=16)
     args = ap.parse_args(argv)

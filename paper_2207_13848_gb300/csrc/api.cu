@@ -200,6 +200,8 @@ DedupArgs dedup_args(const spgemm_csr_t* A, const spgemm_csr_t* B, const Workspa
   d.heavy_cap = A->rows;
   d.heavy_base = 0;
   d.heavy_thr = kWarpCap;
+  d.big_count = nullptr;
+  d.big_thr = 0;
   return d;
 }
 

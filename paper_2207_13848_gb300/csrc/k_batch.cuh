@@ -69,12 +69,18 @@ struct alignas(128) BatchHeader {
   unsigned int heavy_ctr;         // queued rows claimed
   unsigned int tile_ctr;          // FLOP tiles claimed
   unsigned int tiles_done;        // FLOP tiles finished
-  unsigned int pad0[10];
+  unsigned int big_count;         // rows of more than kBatchBigProducts products queued (from the top)
+  unsigned int big_ctr;           // of those, claimed
+  unsigned int pad0[8];
   // flag epoch of the last completed run (only grows)
   unsigned int epoch;
   unsigned int pad1[15];
 };
 constexpr size_t kBatchCounterBytes = 64;  // the leading counters of BatchHeader
+
+// Sampled rows with more products than this go to a second queue that
+// kb_heavy drains first, so the longest rows do not start last.
+constexpr long long kBatchBigProducts = 1ll << 18;
 
 constexpr int kTabRowsPerBlock = 4096;  // B rows per kb_tables block (4 per thread-word, 4 words per thread)
 constexpr int kTabThreads = 256;
@@ -169,6 +175,8 @@ __device__ __forceinline__ void batch_dedup_args(const BatchArgs& b, int c, Dedu
   d.heavy_cap = b.heavy_cap;
   d.heavy_base = (int)k.row_base;
   d.heavy_thr = b.heavy_thr;
+  d.big_count = &b.hdr->big_count;
+  d.big_thr = kBatchBigProducts;
 }
 
 // ---------------------------------------------------------------------------
@@ -278,21 +286,34 @@ __global__ void __launch_bounds__(kDedupThreads) kb_sample(BatchArgs b) {
 }
 
 // ---------------------------------------------------------------------------
-// Heavy rows of all cases, one block per row (see heavy_row_nnz).
+// Heavy rows of all cases, one block per row (see heavy_row_nnz): first the
+// rows of more than kBatchBigProducts products (queued from the top of the
+// array), then the others, each claimed one at a time.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kHeavyThreads) kb_heavy(BatchArgs b, int bitmap_words) {
   extern __shared__ unsigned tab[];
   __shared__ HeavySmem sm;
   __shared__ DedupArgs ha;
-  __shared__ unsigned s_h;
+  __shared__ long long s_h;
   __shared__ int s_case;
   const int t = threadIdx.x;
-  const unsigned n_heavy = (unsigned)min((long long)b.hdr->heavy_count, b.heavy_cap);
+  const unsigned n_big = (unsigned)min((long long)b.hdr->big_count, b.heavy_cap);
+  const unsigned n_heavy = (unsigned)min((long long)b.hdr->heavy_count, b.heavy_cap - n_big);
   for (;;) {
-    if (t == 0) s_h = atomicAdd(&b.hdr->heavy_ctr, 1u);
+    if (t == 0) {
+      long long h = -1;
+      const unsigned q = atomicAdd(&b.hdr->big_ctr, 1u);
+      if (q < n_big) {
+        h = b.heavy_cap - 1 - q;
+      } else {
+        const unsigned r = atomicAdd(&b.hdr->heavy_ctr, 1u);
+        if (r < n_heavy) h = r;
+      }
+      s_h = h;
+    }
     __syncthreads();
-    const unsigned h = s_h;
-    if (h >= n_heavy) break;
+    const long long h = s_h;
+    if (h < 0) break;
     const int g = b.heavy[h] - 1;
     if (t < 32) {
       const int c = warp_last_le(b.n_cases, (long long)g, [&](int i) { return b.cases[i].row_base; });

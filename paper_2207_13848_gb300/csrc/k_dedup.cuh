@@ -51,6 +51,12 @@ struct DedupArgs {
   long long heavy_cap;
   int heavy_base;
   int heavy_thr;
+  // Optional second queue for the largest rows (more than big_thr products),
+  // filled from the top of the same array: heavy[heavy_cap - 1 -
+  // atomicAdd(big_count, 1)].  A consumer that takes these first keeps the
+  // longest rows from being counted last.  big_count == null: one queue.
+  unsigned int* big_count;
+  long long big_thr;
 };
 
 __device__ __forceinline__ uint32_t mix_key(int key) { return (uint32_t)key * 0x9E3779B1u; }
@@ -185,8 +191,15 @@ __device__ long long dedup_row_warp(const DedupArgs& a, int row, int* tbl, long 
   }
 
   if (lane == 0) {
-    const unsigned h = atomicAdd(a.heavy_count, 1u);
-    if (h < (unsigned long long)a.heavy_cap) flag_store(reinterpret_cast<unsigned*>(a.heavy + h), (unsigned)(a.heavy_base + row + 1));
+    const unsigned entry = (unsigned)(a.heavy_base + row + 1);
+    if (a.big_count && flop > a.big_thr) {
+      const unsigned h = atomicAdd(a.big_count, 1u);
+      if (h < (unsigned long long)a.heavy_cap)
+        flag_store(reinterpret_cast<unsigned*>(a.heavy + (a.heavy_cap - 1 - h)), entry);
+    } else {
+      const unsigned h = atomicAdd(a.heavy_count, 1u);
+      if (h < (unsigned long long)a.heavy_cap) flag_store(reinterpret_cast<unsigned*>(a.heavy + h), entry);
+    }
   }
   return -1;
 }

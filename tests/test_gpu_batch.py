@@ -247,3 +247,19 @@ def test_autotune_picks_a_valid_tuning_with_identical_results(small_family):
     for a, b in zip(ref, _batch_outputs(batch)):
         for k in ("pred", "offsets", "flop"):
             np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_batch_with_full_size_cases_matches_oracle():
+    # cases of the family at n = 2^20 (R-MAT with its hub rows, ER, a
+    # rectangular block-diagonal product) among small ones, as in the 625-case
+    # batch: every case bit-exact against the oracle
+    cases = []
+    for st, n, v in (("rmat", 1 << 20, 12), ("er", 1 << 20, 9), ("blockdiag", 1 << 20, 7), ("lap2d", 1 << 12, 3),
+                     ("st27", 1 << 14, 20)):
+        A, B, name = W.family_case(st, n, v)
+        cases.append(dict(_case(A, B, seed=v), name=name))
+    batch = sp.Batch(_device_cases(cases), want_flop=True)
+    batch.run()
+    for c, g in zip(cases, _batch_outputs(batch)):
+        o = oracle_predict(c["A"], c["B"], c["mode"], c["seed"], c["threshold"], c["sample_num"])
+        assert_prediction_equal(g, o, c["name"])
