@@ -285,11 +285,71 @@ struct HeavySmem {
   long long red[kHeavyThreads / 32 + 1];
 };
 
+// The products [p_beg, p_end) of one warp in a group of entries (sm.ex: the
+// entries' exclusive product offsets, with ex[nent] = T; sm.bs: B row start
+// minus the offset), lanes interleaved: each lane keeps its current entry's
+// bounds in registers and reads shared memory only when it crosses into the
+// next entry.  I is the index type: int when the group has fewer than 2^31
+// products (every offset then fits), else long long.  kHeavyUnroll column ids
+// per lane are loaded before any is used, so that many loads of each lane are
+// in flight at once.
+template <bool BITMAP, typename I>
+__device__ __forceinline__ long long heavy_products(const DedupArgs& a, const HeavySmem& sm, int nent, I p_beg,
+                                                    I p_end, unsigned* tab, int lg_or_words, long long lo,
+                                                    long long hi, bool& bad) {
+  const int lane = threadIdx.x & 31;
+  long long cnt = 0;
+  I p = p_beg + lane;
+  if (p_beg >= p_end) return 0;
+  // owner of p: last entry with ex <= p (binary search over nent entries)
+  int lo_i = 0, hi_i = nent;  // ex[lo_i] <= p < ex[hi_i] (for p < T)
+  while (hi_i - lo_i > 1) {
+    const int mid = (lo_i + hi_i) >> 1;
+    if (sm.ex[mid] <= (long long)p) lo_i = mid; else hi_i = mid;
+  }
+  int o = lo_i;
+  I ex_next = (I)sm.ex[o + 1];  // o + 1 <= nent, and ex[nent] = T > every product
+  I base = (I)sm.bs[o];
+  const unsigned lo32 = (unsigned)lo, range = (unsigned)(hi - lo);
+  for (; p < p_end; p += 32 * kHeavyUnroll) {
+    int col[kHeavyUnroll];
+#pragma unroll
+    for (int u = 0; u < kHeavyUnroll; ++u) {
+      const I pu = p + 32 * u;
+      col[u] = -1;
+      if (pu < p_end) {
+        while (pu >= ex_next) {  // into the next non-empty entry
+          ++o;
+          ex_next = (I)sm.ex[o + 1];
+          base = (I)sm.bs[o];
+        }
+        col[u] = __ldg(a.b_col + (base + pu));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kHeavyUnroll; ++u) {
+      if (p + 32 * u >= p_end) continue;
+      const int c = col[u];
+      if (BITMAP) {
+        const unsigned off = (unsigned)c - lo32;
+        if (off < range) {
+          atomicOr(&tab[off >> 5], 1u << (off & 31));
+        } else if ((unsigned)c >= (unsigned long long)a.N) {
+          bad = true;
+        }
+      } else {
+        cnt += table_insert(reinterpret_cast<int*>(tab), lg_or_words, c);
+      }
+    }
+  }
+  return cnt;
+}
+
 template <bool BITMAP, bool COUNT = true>
 __device__ long long heavy_count_pass(const DedupArgs& a, long long rb, long long re, HeavySmem& sm,
                                       unsigned* tab, int lg_or_words, long long lo, long long hi,
                                       bool& bad) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5;
   long long cnt = 0;
   for (long long g = rb; g < re; g += kHeavyThreads) {
     long long s = 0, len = 0;
@@ -304,44 +364,11 @@ __device__ long long heavy_count_pass(const DedupArgs& a, long long rb, long lon
     // warp w takes products [w*Q, (w+1)*Q), Q a multiple of 32
     const long long Q = ((T + 32 * 32 - 1) / (32 * 32)) * 32;
     const long long p_beg = (long long)warp * Q, p_end = min(T, p_beg + Q);
-    long long p = p_beg + lane;
-    if (p_beg < p_end) {
-      // owner of p: last entry with ex <= p (binary search over nent entries)
-      int lo_i = 0, hi_i = nent;  // ex[lo_i] <= p < ex[hi_i] (for p < T)
-      while (hi_i - lo_i > 1) {
-        int mid = (lo_i + hi_i) >> 1;
-        if (sm.ex[mid] <= p) lo_i = mid; else hi_i = mid;
-      }
-      int o = lo_i;
-      // kHeavyUnroll column ids per lane are loaded before any is used, so
-      // that many loads of each lane are in flight at once
-      for (; p < p_end; p += 32 * kHeavyUnroll) {
-        int col[kHeavyUnroll];
-#pragma unroll
-        for (int u = 0; u < kHeavyUnroll; ++u) {
-          const long long pu = p + 32 * u;
-          col[u] = -1;
-          if (pu < p_end) {
-            while (o + 1 < nent && sm.ex[o + 1] <= pu) ++o;
-            col[u] = __ldg(a.b_col + sm.bs[o] + pu);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kHeavyUnroll; ++u) {
-          if (p + 32 * u >= p_end) continue;
-          const int c = col[u];
-          if (BITMAP) {
-            if (c >= lo && c < hi) {
-              const long long off = c - lo;
-              atomicOr(&tab[off >> 5], 1u << (off & 31));
-            } else if ((unsigned)c >= (unsigned long long)a.N) {
-              bad = true;
-            }
-          } else {
-            cnt += table_insert(reinterpret_cast<int*>(tab), lg_or_words, c);
-          }
-        }
-      }
+    if (T < (1ll << 31) - 4096) {  // every offset (and the lanes' lookahead) and B position fits 32 bits
+      cnt += heavy_products<BITMAP, int>(a, sm, nent, (int)min(p_beg, T), (int)p_end, tab, lg_or_words, lo, hi,
+                                         bad);
+    } else {
+      cnt += heavy_products<BITMAP, long long>(a, sm, nent, p_beg, p_end, tab, lg_or_words, lo, hi, bad);
     }
     __syncthreads();
   }
