@@ -587,11 +587,16 @@ def _family_pool(sizes, variants, dev):
 
 
 def run_serve(args):
-    """Serving (continuous admission into stream slots by device memory):
-    saturation throughput, then Poisson arrivals at 0.5x and 0.9x of it;
-    requests mix the five family structures at n = 2^12 .. 2^21 (log-uniform),
-    operands resident on the device, 1 % Bernoulli sample, fresh seed each."""
+    """Serving (continuous batching: admission into stream slots by device
+    memory, small waiting requests merged into batched launches): saturation
+    throughput, then Poisson arrivals at 0.5x and 0.9x of it; requests mix the
+    five family structures at n = 2^12 .. 2^21 (log-uniform), operands resident
+    on the device, 1 % Bernoulli sample, fresh seed each.  Beside it, on the
+    same request stream: one spgemm_predict_structure call per request back to
+    back on one stream (the plain predictor, no server), and the server without
+    merging; every served result record equals the sequential one."""
     import torch
+    import paper_2207_13848_gb300 as sp
     from paper_2207_13848_gb300 import build as spbuild
     from paper_2207_13848_gb300 import serve
     torch.cuda.set_device(0)
@@ -600,24 +605,84 @@ def run_serve(args):
     sizes = [1 << e for e in range(12, 22)]
     pool, names = _family_pool(sizes, (2, 6, 12), dev)
     n = args.serve_requests
-    srv = serve.Server(slots=args.serve_slots, memory_budget=16 << 30, device=dev)
+    T = threshold()
+
+    # the plain predictor, one call per request in arrival order on one stream
+    def sequential(picks):
+        stream = torch.cuda.current_stream()
+        wss = {}
+        outs = []
+        for i, k in enumerate(picks):
+            A, B = pool[k]
+            if k not in wss:
+                wss[k] = sp.Workspace.for_operands(A, B, dev)
+            pred = torch.empty(A.rows, dtype=torch.int32, device=dev)
+            offs = torch.empty(A.rows + 1, dtype=torch.int64, device=dev)
+            outs.append((pred, offs, sp.new_result(dev)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, k in enumerate(picks):
+            A, B = pool[k]
+            pred, offs, res = outs[i]
+            rc = sp.spgemm_predict_structure(A, B, sp.config(threshold=T, seed=i), pred, offs, None, res, wss[k],
+                                             stream)
+            if rc != sp.OK:
+                raise RuntimeError(sp.spgemm_status_string(rc))
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, outs
+
+    if args.serve_sweep:
+        for slots, nst in ((8, 1), (8, 8), (16, 1)):
+            for br in (0, 1 << 16, 1 << 18, 1 << 22):
+                for mb in (128,):
+                    sv = serve.Server(slots=slots, memory_budget=16 << 30, device=dev, batch_rows=br, max_batch=mb,
+                                      streams=nst)
+                    serve.run_poisson(sv, pool, rate=0, n_requests=min(n, 500), seed=99)
+                    d, _ = serve.run_poisson(sv, pool, rate=0, n_requests=n, seed=1)
+                    sm = serve.latency_summary(d)
+                    print(json.dumps({"slots": slots, "streams": nst, "batch_rows": br, "max_batch": mb,
+                                      "req_per_s": n / sm["span"],
+                                      "batched_launches": sv.stats.batched_launches, "launches": sv.stats.launches}))
+        return 0
+    srv = serve.Server(slots=args.serve_slots, memory_budget=16 << 30, device=dev, batch_rows=args.serve_batch_rows,
+                       max_batch=args.serve_max_batch, streams=args.serve_streams)
     serve.run_poisson(srv, pool, rate=0, n_requests=min(n, 500), seed=99)  # warm-up (pools, caches)
-    done, _ = serve.run_poisson(srv, pool, rate=0, n_requests=n, seed=1)
+    done, picks = serve.run_poisson(srv, pool, rate=0, n_requests=n, seed=1)
     sat = serve.latency_summary(done)
     sat_rate = n / sat["span"]
+    sequential(picks[:200])  # warm-up
+    t_seq, seq_out = sequential(picks)
+    seq_rate = n / t_seq
+    seq_res = torch.stack([o[2] for o in seq_out]).cpu().tolist()
+    same = all([int(x) for x in r.res_host.tolist()] == seq_res[r.index] for r in done)
+    nomerge = serve.Server(slots=args.serve_slots, memory_budget=16 << 30, device=dev, batch_rows=0,
+                           streams=args.serve_streams)
+    serve.run_poisson(nomerge, pool, rate=0, n_requests=min(n, 500), seed=99)
+    done_nm, _ = serve.run_poisson(nomerge, pool, rate=0, n_requests=n, seed=1)
+    nm = serve.latency_summary(done_nm)
     levels = [{"offered": "all at once", **sat, "req_per_s": sat_rate}]
     for f in (0.5, 0.9):
-        done, _ = serve.run_poisson(srv, pool, rate=f * sat_rate, n_requests=n, seed=int(10 * f))
-        summ = serve.latency_summary(done)
+        done_f, _ = serve.run_poisson(srv, pool, rate=f * sat_rate, n_requests=n, seed=int(10 * f))
+        summ = serve.latency_summary(done_f)
         levels.append({"offered": f"{f} x saturation", "offered_req_per_s": f * sat_rate, **summ,
                        "req_per_s": n / summ["span"]})
+    done_f, _ = serve.run_poisson(srv, pool, rate=5000.0, n_requests=n, seed=50)  # a fixed absolute load
+    summ = serve.latency_summary(done_f)
+    levels.append({"offered": "5000 req/s", "offered_req_per_s": 5000.0, **summ, "req_per_s": n / summ["span"]})
     bad = [r for r in srv.finished if int(r.res_host[5]) & 0x300]
     line = {"suite": "serve", "metric": "requests/s and p50/p99 latency of served predictions",
-            "n_requests": n, "slots": args.serve_slots, "pool": len(pool),
-            "pool_sizes": "n = 2^12..2^21, 5 structures", "peak_inflight": srv.stats.peak_inflight,
-            "error_results": len(bad), "levels": levels}
+            "n_requests": n, "slots": args.serve_slots, "streams": args.serve_streams, "pool": len(pool),
+            "pool_sizes": "n = 2^12..2^21, 5 structures", "batch_rows": srv.batch_rows, "max_batch": srv.max_batch,
+            "peak_inflight": srv.stats.peak_inflight, "launches": srv.stats.launches,
+            "batched_launches": srv.stats.batched_launches, "batched_requests": srv.stats.batched_requests,
+            "error_results": len(bad), "failed": srv.stats.failed, "levels": levels,
+            "sequential_plain_predictor": {"req_per_s": seq_rate, "s": t_seq,
+                                           "how": "one spgemm_predict_structure per request, same operands and "
+                                                  "seeds, back to back on one stream"},
+            "server_without_merging": {"req_per_s": n / nm["span"], "p50": nm["p50"], "p99": nm["p99"]},
+            "speedup_vs_sequential": sat_rate / seq_rate, "identical_to_sequential": same}
     print(json.dumps(line))
-    return 0
+    return 0 if same else 1
 
 
 def run_batch(args):
@@ -865,7 +930,12 @@ def main(argv=None):
     ap.add_argument("--batch-sizes", type=int, nargs="+", default=[12, 14, 16, 18, 20],
                     help="log2 of the family's sizes for --suite batch (default: all five, 625 cases)")
     ap.add_argument("--serve-requests", type=int, default=10000)
-    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-batch-rows", type=int, default=1 << 18,
+                    help="requests with at most this many rows are merged into batched launches")
+    ap.add_argument("--serve-max-batch", type=int, default=128)
+    ap.add_argument("--serve-streams", type=int, default=1, help="CUDA streams the slots run on")
+    ap.add_argument("--serve-sweep", action="store_true", help="only the saturation rate for a grid of settings")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

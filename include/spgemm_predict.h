@@ -29,8 +29,11 @@
  *     thread scheduling or the GPU model.
  *   - The workspace must be zero-filled before its first use and is left
  *     reusable by every call that ends with a status free of SPGEMM_STATUS_ERR_*
- *     bits; after such an error, zero it again.  Calls that share one workspace
- *     must not overlap in time (queue them on one stream).
+ *     bits, for any later call whose operands it is large enough for (the
+ *     regions that must start from zero sit at fixed offsets); after such an
+ *     error, zero it again.  Calls that share one workspace must not overlap in
+ *     time (queue them on one stream).  A batch workspace (spgemm_batch_*) is
+ *     a different layout and is not interchangeable with this one.
  */
 #ifndef SPGEMM_PREDICT_H
 #define SPGEMM_PREDICT_H
@@ -257,6 +260,18 @@ typedef struct spgemm_batch_item {
   int32_t* flop_row;        /* int32[A.rows], or NULL */
   spgemm_result_t* res;     /* one record per case */
 } spgemm_batch_item_t;
+
+/* Many single predictions queued by one call (a library utility; the paper has
+ * no counterpart): for i = 0 .. n-1 in order, the spgemm_predict_structure call
+ * of items[i] (its operands, configuration and outputs) with the workspace
+ * ws[i] of ws_bytes[i] bytes, all on `stream`.  For a host that issues many
+ * predictions (a serving loop), this replaces n calls across a language
+ * boundary with one; each prediction is still its own launch, with results
+ * bit-identical to spgemm_predict_structure.  Returns SPGEMM_OK, or the code of
+ * the first call whose host checks fail, with *bad_item = its index (when
+ * bad_item is not NULL): the calls before it were queued, none after it. */
+int spgemm_predict_many(const spgemm_batch_item_t* items, int32_t n, void* const* ws, const size_t* ws_bytes,
+                        int32_t* bad_item, void* stream);
 
 /* Launch parameters of the batch; they change speed, never results.  0 selects
  * the default.  spgemm_batch_autotune measures candidates and picks one. */

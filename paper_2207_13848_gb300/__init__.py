@@ -118,6 +118,9 @@ def load():
     lib.spgemm_predict_structure_static.restype = ctypes.c_int
     lib.spgemm_set_profile_events.argtypes = [P, P]
     lib.spgemm_set_profile_events.restype = ctypes.c_int
+    lib.spgemm_predict_many.argtypes = [ctypes.POINTER(BatchItemStruct), ctypes.c_int32, ctypes.POINTER(P),
+                                        ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_int32), P]
+    lib.spgemm_predict_many.restype = ctypes.c_int
     lib.spgemm_lookup_probe.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, P, P]
     lib.spgemm_lookup_probe.restype = ctypes.c_int
     I = ctypes.POINTER(BatchItemStruct)
@@ -316,6 +319,13 @@ def spgemm_set_profile_events(before, after):
     b = None if before is None else ctypes.c_void_p(before.cuda_event)
     a = None if after is None else ctypes.c_void_p(after.cuda_event)
     return load().spgemm_set_profile_events(b, a)
+
+
+def spgemm_predict_many(items, n, ws_ptrs, ws_bytes, bad_item, stream=None):
+    """items: ctypes array of BatchItemStruct; ws_ptrs: ctypes array of c_void_p;
+    ws_bytes: ctypes array of c_size_t; bad_item: ctypes.c_int32 or None."""
+    return load().spgemm_predict_many(items, int(n), ws_ptrs, ws_bytes,
+                                      ctypes.byref(bad_item) if bad_item is not None else None, _stream(stream))
 
 
 def spgemm_lookup_probe(col, table, out, stream=None):

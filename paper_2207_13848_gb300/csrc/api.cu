@@ -587,6 +587,9 @@ int batch_prepare(const spgemm_batch_item_t* items, int n, const spgemm_batch_tu
   if (cudaMemcpyAsync(dev + l.cases, buf, l.plan_bytes(), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return SPGEMM_ERR_CUDA;
   if (cudaMemsetAsync(dev + l.acc, 0, sizeof(CaseAcc) * (size_t)n, st) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  // the tile slots of this plan may lie where another plan kept other data:
+  // their flags start from zero
+  if (cudaMemsetAsync(dev + l.slots, 0, sizeof(Slot) * (size_t)T.tiles, st) != cudaSuccess) return SPGEMM_ERR_CUDA;
   if (!host_staging && cudaStreamSynchronize(st) != cudaSuccess) return SPGEMM_ERR_CUDA;
   spgemm_batch_plan_t p{};
   p.n_cases = n;
@@ -964,6 +967,21 @@ int spgemm_batch_autotune(const spgemm_batch_item_t* items, int32_t n, void* ws,
   if (rc) return rc;
   *best = pick;
   if (best_ms) *best_ms = total;
+  return SPGEMM_OK;
+}
+
+int spgemm_predict_many(const spgemm_batch_item_t* items, int32_t n, void* const* ws, const size_t* ws_bytes,
+                        int32_t* bad_item, void* stream) {
+  if (!items || n < 0 || (n > 0 && (!ws || !ws_bytes))) return SPGEMM_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n; ++i) {
+    const spgemm_batch_item_t& it = items[i];
+    const int rc = predict_common(&it.A, &it.B, &it.cfg, it.pred_row, it.offsets, it.flop_row, it.res, ws[i],
+                                  ws_bytes[i], stream, false);
+    if (rc != SPGEMM_OK) {
+      if (bad_item) *bad_item = i;
+      return rc;
+    }
+  }
   return SPGEMM_OK;
 }
 

@@ -88,11 +88,17 @@ constexpr size_t ws_round(size_t b) { return ((b + 255) / 256) * 256; }
 constexpr long long ws_huge_words(int64_t N) { return N > 0 ? (N + 2047) / 2048 * 64 : 0; }
 
 // Bytes for M rows of A, K columns of A (= rows of B) and N columns of B (the
-// split-row bitmaps; N = 0 leaves them out).
+// split-row bitmaps; N = 0 leaves them out).  The regions that must read as
+// zero when a call starts (header, block slots, split-row slots) sit at fixed
+// offsets, so a workspace left clean by one call is clean for any later call
+// whose operands it is large enough for, whatever their shapes; the regions
+// whose place depends on M, K and N are written by a call before it reads them
+// (the heavy-row queue is read only below the count of entries queued).
 constexpr size_t ws_bytes_for(int64_t M, int64_t K, int64_t N = 0) {
   const size_t m = (size_t)(M > 0 ? M : 1), k = (size_t)(K > 0 ? K : 1);
-  size_t b = sizeof(WsHeader) + sizeof(Slot) * kMaxSlots + 2 * ws_round(m * 4) + ws_round(k + 16);
-  if (N > 0) b += sizeof(HugeSlot) * kHugeSlots + (size_t)kHugeSlots * kMaxParts * (size_t)ws_huge_words(N) * 4;
+  size_t b = sizeof(WsHeader) + sizeof(Slot) * kMaxSlots + sizeof(HugeSlot) * kHugeSlots + 2 * ws_round(m * 4) +
+             ws_round(k + 16);
+  if (N > 0) b += (size_t)kHugeSlots * kMaxParts * (size_t)ws_huge_words(N) * 4;
   return b;
 }
 
@@ -104,14 +110,14 @@ inline Workspace ws_carve(void* base, int64_t M, int64_t K = 0, int64_t N = 0) {
   p += sizeof(WsHeader);
   w.slots = reinterpret_cast<Slot*>(p);
   p += sizeof(Slot) * kMaxSlots;
+  w.huge = N > 0 ? reinterpret_cast<HugeSlot*>(p) : nullptr;
+  p += sizeof(HugeSlot) * kHugeSlots;
   w.heavy = reinterpret_cast<int*>(p);
   p += ws_round(m * 4);
   w.flop_buf = reinterpret_cast<int*>(p);
   p += ws_round(m * 4);
   w.deg8 = reinterpret_cast<unsigned char*>(p);
   p += ws_round(k + 16);
-  w.huge = N > 0 ? reinterpret_cast<HugeSlot*>(p) : nullptr;
-  p += sizeof(HugeSlot) * kHugeSlots;
   w.hbits = N > 0 ? reinterpret_cast<unsigned int*>(p) : nullptr;
   w.huge_words = ws_huge_words(N);
   return w;

@@ -402,7 +402,10 @@ __device__ int claim_heavy_row(WsHeader* hdr, int* heavy, unsigned long long cap
   const uint64_t t0 = global_ns();
   unsigned ns = 32;
   for (int it = 0; it < (1 << 26); ++it) {
-    if (h < cap) {
+    // only entries below the count queued so far exist (a clean workspace may
+    // hold anything past them); an existing entry reads 0 until its writer's
+    // store lands
+    if (h < cap && h < flag_load(&hdr->heavy_count)) {
       const unsigned v = flag_load(reinterpret_cast<const unsigned*>(heavy + h));
       if (v != 0) {
         heavy[h] = 0;  // taken

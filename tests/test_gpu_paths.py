@@ -97,3 +97,38 @@ def test_lookup_probe_sums_the_bytes_it_reads():
     assert sp.spgemm_lookup_probe(dcol, dtab, out) == sp.OK
     torch.cuda.synchronize()
     assert int(out.item()) == want
+
+
+def test_predict_many_equals_single_calls_and_stops_at_a_rejected_item():
+    # spgemm_predict_many queues the single-case calls of many items by one
+    # host call: outputs bit-identical to spgemm_predict_structure; a call
+    # rejected on the host stops it there (the calls before it were queued)
+    import ctypes
+    mats = [W.erdos_renyi(3000, 7, 1), W.rmat(12, 8, seed=2), W.laplacian_2d(40)]
+    dev = [to_dev(m) for m in mats]
+    T = int(0.05 * TWO32)
+    n = 4
+    items = (sp.BatchItemStruct * n)()
+    outs, wss = [], []
+    ptrs, sizes = (ctypes.c_void_p * n)(), (ctypes.c_size_t * n)()
+    for i in range(n):
+        dA = dev[i % 3]
+        cfg = sp.config(threshold=T, seed=i) if i != 2 else sp.config(threshold=(1 << 32) + 1)
+        pred, offs, res = (torch.empty(dA.rows, dtype=torch.int32, device="cuda"),
+                           torch.empty(dA.rows + 1, dtype=torch.int64, device="cuda"), sp.new_result("cuda"))
+        outs.append((pred, offs, res))
+        it = items[i]
+        it.A, it.B, it.cfg = dA.struct(), dA.struct(), cfg
+        it.pred_row, it.offsets, it.flop_row, it.res = pred.data_ptr(), offs.data_ptr(), None, res.data_ptr()
+        ws = sp.Workspace.for_operands(dA, dA)
+        wss.append(ws)
+        ptrs[i], sizes[i] = ws.view.data_ptr(), ws.nbytes
+    bad = ctypes.c_int32(-1)
+    rc = sp.spgemm_predict_many(items, n, ptrs, sizes, bad)
+    torch.cuda.synchronize()
+    assert rc == sp.ERR_INVALID_ARG and bad.value == 2
+    for i in range(2):
+        o = oracle_predict(mats[i], mats[i], oracle.BERNOULLI, i, T)
+        g = dict(pred=outs[i][0].cpu().numpy(), offsets=outs[i][1].cpu().numpy(), flop=o["flop"],
+                 **sp.read_result(outs[i][2]))
+        assert_prediction_equal(g, o, f"item {i}")

@@ -18,40 +18,79 @@ class _Ev:
 
 
 class StubServer(serve.Server):
-    """Server without a GPU: launches record an event the test fires by hand."""
+    """Server without a GPU: launches record an event the test fires by hand.
+    `rows` gives each operand's row count (for the small-request test); an
+    operand missing from it is never merged."""
 
-    def __init__(self, slots, budget, sizes):
+    def __init__(self, slots, budget, sizes, rows=None, batch_rows=0, max_batch=64):
         self.streams = [None] * slots
         self.free_slots = collections.deque(range(slots))
         self.budget = budget
+        self.batch_rows = batch_rows
+        self.max_batch = max_batch
         self.used = 0
-        self.waiting = collections.deque()
+        self.wait_small = collections.deque()
+        self.wait_large = collections.deque()
         self.inflight = {}
         self.finished = []
+        self.failed = []
         self.pool = collections.defaultdict(list)
+        self.bpool = collections.defaultdict(list)
+        self.staging_pool = collections.defaultdict(list)
         self.stats = serve._Stats()
         self._next_id = 0
+        self._next_launch = 0
         self.sizes = sizes
+        self.rows = rows or {}
         self.launched = []
+        self.fail_next = False
 
     def request_bytes(self, A, B):
         return self.sizes[A]
 
-    def _launch(self, r):
-        r.slot = self.free_slots.popleft()
-        self.used += r.nbytes
-        r._event = _Ev()
-        self.inflight[r.rid] = r
-        self.launched.append(r.rid)
-        self.stats.admitted += 1
-        self.stats.peak_inflight = max(self.stats.peak_inflight, len(self.inflight))
-        self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
+    def _small(self, r):
+        return self.batch_rows > 0 and not r.solo and self.rows.get(r.A, 1 << 40) <= self.batch_rows
 
-    def _retire(self, r):
-        self.used -= r.nbytes
-        self.free_slots.append(r.slot)
-        self.finished.append(r)
-        self.stats.finished += 1
+    def _begin(self, ln):
+        ln.event = _Ev()
+        self.inflight[self._next_launch] = ln
+        self._next_launch += 1
+        self.used += ln.nbytes
+        self.stats.admitted += len(ln.requests)
+        self.stats.peak_inflight = max(self.stats.peak_inflight, sum(len(x.requests) for x in self.inflight.values()))
+        self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
+        self.launched.append([r.rid for r in ln.requests])
+
+    def _launch_many(self, group, nbytes):
+        slot = self.free_slots.popleft()
+        if self.fail_next:  # the first request's call is rejected: it fails, the rest wait again
+            self.fail_next = False
+            for r in reversed(group[1:]):
+                self.wait_large.appendleft(r)
+            self._fail(serve._Launch(group[:1], slot, group[0].nbytes), None, "rejected by the stub")
+            return
+        for r in group:
+            r.slot = slot
+        self._begin(serve._Launch(group, slot, nbytes))
+
+    def _launch_batch(self, group, nbytes):
+        slot = self.free_slots.popleft()
+        for r in group:
+            r.slot, r.batched = slot, True
+        self._begin(serve._Launch(group, slot, nbytes, batch=True))
+
+    def _retire(self, ln):
+        self.used -= ln.nbytes
+        self.free_slots.append(ln.slot)
+        self.finished.extend(ln.requests)
+        self.stats.finished += len(ln.requests)
+        return len(ln.requests)
+
+
+def fire(srv, *reqs):
+    for ln in srv.inflight.values():
+        if any(r in ln.requests for r in reqs):
+            ln.event.fired = True
 
 
 def test_admission_follows_arrival_order_slots_and_budget():
@@ -61,13 +100,14 @@ def test_admission_follows_arrival_order_slots_and_budget():
     rc = srv.submit("c", None, None, arrival=0.2)
     assert srv.submit("huge", None, None) is None and srv.stats.rejected == 1
     srv.poll()
-    assert srv.launched == [ra.rid, rb.rid]      # two slots, 90 bytes <= 100
+    # requests that wait together go out in one launch while they fit: 90 bytes <= 100
+    assert srv.launched == [[ra.rid, rb.rid]]
     assert srv.used == 90 and list(srv.waiting) == [rc]
-    ra._event.fired = True
-    srv.poll()                                   # a retires: slot and 60 bytes back; c (50) fits
-    assert srv.launched == [ra.rid, rb.rid, rc.rid]
-    assert srv.used == 80 and srv.stats.peak_bytes <= 100
-    rb._event.fired = rc._event.fired = True
+    fire(srv, ra)
+    srv.poll()                                   # a and b retire: 90 bytes back; c (50) fits
+    assert srv.launched == [[ra.rid, rb.rid], [rc.rid]]
+    assert srv.used == 50 and srv.stats.peak_bytes <= 100
+    fire(srv, rc)
     srv.poll()
     assert srv.used == 0 and not srv.inflight and srv.stats.finished == 3
 
@@ -79,10 +119,62 @@ def test_head_of_line_waits_for_memory():
     rz = srv.submit("z", None, None)
     srv.poll()
     # y does not fit beside x; admission is in arrival order, so z waits behind y
-    assert srv.launched == [rx.rid] and list(srv.waiting) == [ry, rz]
-    rx._event.fired = True
+    assert srv.launched == [[rx.rid]] and list(srv.waiting) == [ry, rz]
+    fire(srv, rx)
     srv.poll()
-    assert srv.launched == [rx.rid, ry.rid, rz.rid]
+    assert srv.launched == [[rx.rid], [ry.rid, rz.rid]]
+
+
+def test_small_requests_waiting_together_share_one_launch():
+    # continuous batching: small requests at the head of the queue are merged,
+    # in arrival order, into one launch on one slot; a large one goes alone
+    srv = StubServer(slots=2, budget=1000, sizes={"s": 10, "L": 100}, rows={"s": 64, "L": 10 ** 6},
+                     batch_rows=1024)
+    rs = [srv.submit(k, None, None) for k in ("s", "s", "s", "L", "s", "s")]
+    srv.poll()
+    # the small requests are merged whatever large one arrived between them;
+    # the large one goes alone on the other slot
+    assert srv.launched == [[0, 1, 2, 4, 5], [3]] and not srv.waiting
+    assert all(r.batched for r in rs if r.A == "s") and not rs[3].batched
+    fire(srv, rs[0])
+    srv.poll()
+    assert srv.stats.finished == 5 and srv.used == 100
+    rl = srv.submit("L", None, None)
+    rsm = srv.submit("s", None, None)
+    srv.poll()                                   # the freed slot takes the earlier arrival: the large one
+    assert srv.launched[-1] == [rl.rid] and srv.waiting == [rsm]
+    fire(srv, *rs, rl)
+    srv.poll()
+    assert srv.launched[-1] == [rsm.rid]
+    fire(srv, rsm)
+    srv.poll()
+    assert srv.stats.finished == 8 and srv.used == 0
+
+
+def test_batches_respect_max_batch_and_the_budget():
+    srv = StubServer(slots=3, budget=35, sizes={"s": 10}, rows={"s": 1}, batch_rows=8, max_batch=2)
+    rs = [srv.submit("s", None, None) for _ in range(5)]
+    srv.poll()
+    # at most two per launch, and 35 bytes hold three requests at once
+    assert srv.launched == [[0, 1], [2]] and srv.used == 30
+    fire(srv, *rs)
+    srv.poll()
+    assert srv.launched[2:] == [[3, 4]]
+
+
+def test_a_rejected_launch_does_not_stop_the_loop():
+    srv = StubServer(slots=1, budget=100, sizes={"a": 10, "b": 10})
+    srv.fail_next = True
+    ra = srv.submit("a", None, None)
+    rb = srv.submit("b", None, None)
+    srv.poll()
+    # a's call was rejected: it is marked failed, its slot and memory are back,
+    # and b was admitted again on the same poll
+    assert ra.error and srv.failed == [ra] and srv.stats.failed == 1 and srv.stats.rejected == 1
+    assert srv.launched == [[rb.rid]] and srv.used == 10
+    fire(srv, rb)
+    srv.poll()
+    assert srv.finished == [rb] and srv.used == 0 and len(srv.free_slots) == 1
 
 
 def test_latency_summary():
