@@ -757,35 +757,40 @@ def run_accuracy(args):
     (Z1*) over the synthetic family, as in Sec. VI-A: per case the exact Z from
     the GPU symbolic phase, then mean / worst |eps1|, |eps_f|, |eps2|, the share
     of cases where eps2 beats eps1 and corr(eps1, eps_f), for the 1 % Bernoulli
-    sample and the paper's min(0.003 M, 300) draws."""
+    sample and the paper's min(0.003 M, 300) draws; over all 625 cases (5
+    structures x n = 2^12..2^20 x 25 variants) and per size."""
     import torch
     import paper_2207_13848_gb300 as sp
     from paper_2207_13848_gb300 import build as spbuild
     from paper_2207_13848_gb300.report import accuracy_summary, estimates
+    exps = tuple(args.batch_sizes)
+    fam = family_cases([1 << e for e in exps])  # before the first CUDA call (spawned workers)
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     spbuild.build()
     per_mode = {"bernoulli_1pct": [], "paper_draws": []}
-    for st in W.STRUCTURES:
-        for e in (12, 14, 16):
-            for v in range(25):
-                A, B, name = W.family_case(st, 1 << e, v)
-                dA = sp.DeviceCSR.from_host(A, dev)
-                dB = dA if B is A else sp.DeviceCSR.from_host(B, dev)
-                ws = sp.Workspace.for_operands(dA, dB, dev)
-                Z = sp.read_result(sp.symbolic_exact(dA, dB, ws=ws).res)["pred_total"]
-                for mode, cfg in (("bernoulli_1pct", sp.config(threshold=threshold(), seed=v)),
-                                  ("paper_draws", sp.config(mode=sp.SAMPLE_PAPER_DRAW, seed=v))):
-                    r = sp.read_result(sp.predict_structure(dA, dB, cfg, ws=ws).res)
-                    est = estimates(r["flop_total"], Z, r["flop_s"], r["nnz_s"], A.rows, r["n_sampled"])
-                    per_mode[mode].append(dict(case=name, **est))
+    by_size = {}
+    for st, n, v, A, B, name in fam:
+        dA = sp.DeviceCSR.from_host(A, dev)
+        dB = dA if B is A else sp.DeviceCSR.from_host(B, dev)
+        ws = sp.Workspace.for_operands(dA, dB, dev)
+        Z = sp.read_result(sp.symbolic_exact(dA, dB, ws=ws).res)["pred_total"]
+        for mode, cfg in (("bernoulli_1pct", sp.config(threshold=threshold(), seed=v)),
+                          ("paper_draws", sp.config(mode=sp.SAMPLE_PAPER_DRAW, seed=v))):
+            r = sp.read_result(sp.predict_structure(dA, dB, cfg, ws=ws).res)
+            est = estimates(r["flop_total"], Z, r["flop_s"], r["nnz_s"], A.rows, r["n_sampled"])
+            per_mode[mode].append(dict(case=name, **est))
+            by_size.setdefault((mode, n), []).append(dict(case=name, **est))
+        del dA, dB, ws
     line = {"suite": "accuracy", "metric": "relative error of the predicted NNZ(C), Sec. VI-A statistics",
-            "cases": "5 structures x n=2^12,2^14,2^16 x 25 variants (375), exact Z from the GPU symbolic phase",
+            "cases": f"5 structures x n={','.join(f'2^{e}' for e in exps)} x 25 variants ({len(fam)}), "
+                     "exact Z from the GPU symbolic phase",
             "paper_context": {"mean_abs": {"eps1": 0.0812, "eps_f": 0.0859, "eps2": 0.0156},
                               "max_abs": {"eps1": 1.58, "eps_f": 1.55, "eps2": 0.25},
                               "eps2_better_share": 0.814, "corr_eps1_epsf": 0.9701,
                               "note": "625 SuiteSparse cross-products on CPUs; context only"},
-            "results": {m: accuracy_summary(c) for m, c in per_mode.items()}}
+            "results": {m: accuracy_summary(c) for m, c in per_mode.items()},
+            "by_size": {f"{m} n=2^{n.bit_length() - 1}": accuracy_summary(c) for (m, n), c in sorted(by_size.items())}}
     print(json.dumps(line))
     return 0
 
