@@ -448,9 +448,9 @@ def predict_cr(A, B, cfg, ws=None, stream=None):
 
 def sample_rows(rows, cfg, capacity=None, ws=None, device="cuda", stream=None):
     torch = _torch()
-    cap = rows if capacity is None else capacity
-    if cfg.mode == SAMPLE_PAPER_DRAW:
-        cap = max(cap, cfg.sample_num if cfg.sample_num else min(max(3 * rows // 1000, 1), 300))
+    # |S| <= rows in both modes (the library takes at most `rows` draws), so a
+    # buffer of `rows` ids always holds the sample
+    cap = max(rows, 1) if capacity is None else capacity
     ws = ws or Workspace(_build_ws_bytes(rows), device)
     ids = torch.full((max(cap, 1),), -1, dtype=torch.int32, device=device)
     res = new_result(device)
