@@ -39,7 +39,9 @@ namespace spg {
 
 constexpr int kPredThreads = 1024;
 constexpr int kPredWarps = kPredThreads / 32;
-constexpr long long kPredItemsPerBlock = 16384;  // merged items per block, at least
+// merged items per block, at least: small problems get more blocks, so each
+// block's chains of round trips are short (2D 5-point 64x64: 37 -> 29 us)
+constexpr long long kPredItemsPerBlock = 1024;
 static_assert(kPredThreads == kHeavyThreads, "heavy rows are counted by the whole block");
 
 // ---- the two warp groups --------------------------------------------------------
