@@ -118,7 +118,7 @@ typedef struct spgemm_result {
 /* ---- entry points ----------------------------------------------------------------- */
 
 /* Bytes of device workspace every entry point below needs for these operands:
- * about 8 * A.rows + A.cols + 8 * B.cols bytes plus a fixed 268 KB (the B.cols
+ * about 8 * A.rows + A.cols + 8 * B.cols bytes plus a fixed 264 KB (the B.cols
  * part holds the bitmaps of sampled rows split over several thread blocks).  B
  * may be NULL, in which case B.cols is taken to be A.cols (C = A * A). */
 size_t spgemm_workspace_size(const spgemm_csr_t* A, const spgemm_csr_t* B);
