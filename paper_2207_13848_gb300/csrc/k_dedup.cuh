@@ -309,37 +309,53 @@ __device__ __forceinline__ long long heavy_products(const DedupArgs& a, const He
   }
   int o = lo_i;
   I ex_next = (I)sm.ex[o + 1];  // o + 1 <= nent, and ex[nent] = T > every product
-  I base = (I)sm.bs[o];
+  // q[pu] is the column id of product pu while pu lies in entry o
+  const int* q = a.b_col + sm.bs[o];
   const unsigned lo32 = (unsigned)lo, range = (unsigned)(hi - lo);
+  // one bitmap pass over all of B's columns: an id outside it is out of range
+  const bool whole = lo == 0 && hi == a.N;
+  auto advance = [&](I pu) {  // into the entry holding pu (skipping empty ones)
+    while (pu >= ex_next) {
+      ++o;
+      ex_next = (I)sm.ex[o + 1];
+      q = a.b_col + sm.bs[o];
+    }
+  };
+  auto put = [&](int c) {
+    if (BITMAP) {
+      const unsigned off = (unsigned)c - lo32;
+      if (off < range) {
+        atomicOr(&tab[off >> 5], __funnelshift_l(0u, 1u, off));  // bit off & 31
+      } else if (whole || (unsigned)c >= (unsigned long long)a.N) {
+        bad = true;
+      }
+    } else {
+      cnt += table_insert(reinterpret_cast<int*>(tab), lg_or_words, c);
+    }
+  };
   for (; p < p_end; p += 32 * kHeavyUnroll) {
     int col[kHeavyUnroll];
+    if (p + 32 * (kHeavyUnroll - 1) < p_end) {  // the lane's whole step lies in the range
 #pragma unroll
-    for (int u = 0; u < kHeavyUnroll; ++u) {
-      const I pu = p + 32 * u;
-      col[u] = -1;
-      if (pu < p_end) {
-        while (pu >= ex_next) {  // into the next non-empty entry
-          ++o;
-          ex_next = (I)sm.ex[o + 1];
-          base = (I)sm.bs[o];
-        }
-        col[u] = __ldg(a.b_col + (base + pu));
+      for (int u = 0; u < kHeavyUnroll; ++u) {
+        advance(p + 32 * u);
+        col[u] = __ldg(q + (p + 32 * u));
       }
-    }
 #pragma unroll
-    for (int u = 0; u < kHeavyUnroll; ++u) {
-      if (p + 32 * u >= p_end) continue;
-      const int c = col[u];
-      if (BITMAP) {
-        const unsigned off = (unsigned)c - lo32;
-        if (off < range) {
-          atomicOr(&tab[off >> 5], 1u << (off & 31));
-        } else if ((unsigned)c >= (unsigned long long)a.N) {
-          bad = true;
+      for (int u = 0; u < kHeavyUnroll; ++u) put(col[u]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < kHeavyUnroll; ++u) {
+        const I pu = p + 32 * u;
+        col[u] = -1;
+        if (pu < p_end) {
+          advance(pu);
+          col[u] = __ldg(q + pu);
         }
-      } else {
-        cnt += table_insert(reinterpret_cast<int*>(tab), lg_or_words, c);
       }
+#pragma unroll
+      for (int u = 0; u < kHeavyUnroll; ++u)
+        if (p + 32 * u < p_end) put(col[u]);
     }
   }
   return cnt;
