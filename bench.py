@@ -733,6 +733,16 @@ def run_batch(args):
     t_per = timed(per_case, steps)
     batch = sp.Batch(cases, device=dev)
     best, best_ms = batch.autotune(reps=3)
+    # both forms with the tuned phases: one persistent launch, one launch per phase
+    forms = {}
+    for launches in (1, 4):
+        tu = sp.tuning(**dict(best.as_dict(), launches=launches))
+        batch.prepare(tu)
+        batch.run()
+        t_f = timed(batch.run, steps)
+        forms[f"{launches}_launch" + ("es" if launches > 1 else "")] = {"median_ms": t_f[len(t_f) // 2],
+                                                                        "tuning": tu.as_dict()}
+    batch.prepare(best)
     batch.run()
     t_batch = timed(batch.run, steps)
     # same integers: every case's result record and offsets[M]
@@ -747,7 +757,7 @@ def run_batch(args):
             "batch_ms": {"median": t_batch[len(t_batch) // 2], "min": t_batch[0]},
             "speedup_median": t_per[len(t_per) // 2] / t_batch[len(t_batch) // 2],
             "tuning": best.as_dict(), "autotune_ms": best_ms, "identical_results": same,
-            "gpu_launches_per_pass": {"per_case": len(cases), "batch": 4}}
+            "forms": forms, "gpu_launches_per_pass": {"per_case": len(cases), "batch": best.launches}}
     print(json.dumps(line))
     return 0 if same else 1
 

@@ -234,9 +234,9 @@ int spgemm_predict_structure_static(const spgemm_csr_t* A, const spgemm_csr_t* B
 /* ---- batched prediction ---------------------------------------------------------------
  * Many independent predictions ("cases") of uneven sizes computed together: the
  * paper's method (Eq. 4, Algorithm 2) for every case, exactly as
- * spgemm_predict_structure computes it, but as one set of four persistent
- * launches that span the whole batch, so small cases share the GPU instead of
- * each paying the latency of its own launches.  The paper predicts one product
+ * spgemm_predict_structure computes it, but as one persistent launch (or, by
+ * tuning, four: one per phase) that spans the whole batch, so small cases share
+ * the GPU instead of each paying the latency of its own launches.  The paper predicts one product
  * at a time; batching is a library feature for callers with many products.
  * Per case, every output (pred_row, offsets, flop_row, the result record) is
  * bit-identical to spgemm_predict_structure with the same arguments, whatever
@@ -285,8 +285,13 @@ typedef struct spgemm_batch_tuning {
   int32_t sample_chunk;       /* candidates per unit of work of the sampled-row pass, a
                                  multiple of 256 in [4096, 2^24]; default 32768 */
   int32_t flop_blocks_per_sm; /* resident blocks per SM of the FLOP pass, 1 .. what fits;
-                                 default what fits */
-  int32_t reserved[3];        /* must be 0 */
+                                 default what fits (used by launches = 4) */
+  int32_t launches;           /* 1: the whole batch as one persistent launch (one block per SM,
+                                 grid barriers between the phases); 4: one persistent launch per
+                                 phase (tables, sampled rows, heavy rows, FLOP and offsets), each
+                                 with its own shared-memory size and block shape; default 4, the
+                                 faster at scale (625 family cases: 34.8 against 43.9 ms) */
+  int32_t reserved[2];        /* must be 0 */
 } spgemm_batch_tuning_t;
 
 /* What spgemm_batch_prepare planned; pass it to spgemm_predict_batch. */
@@ -328,8 +333,9 @@ int spgemm_batch_prepare(const spgemm_batch_item_t* items, int32_t n,
                          void* ws, size_t ws_bytes, void* host_staging, size_t staging_bytes,
                          int32_t* bad_item, void* stream);
 
-/* Runs the prepared batch on `stream`: four kernel launches and one 64-byte
- * memset, no host synchronisation, capturable in a CUDA graph.  Every case's
+/* Runs the prepared batch on `stream`: one 64-byte memset and one cooperative
+ * kernel launch (tuning.launches = 1) or four launches (4), no host
+ * synchronisation, capturable in a CUDA graph.  Every case's
  * outputs and result record are written as by spgemm_predict_structure;
  * result status bits are per case. */
 int spgemm_predict_batch(const spgemm_batch_plan_t* plan, void* ws, size_t ws_bytes, void* stream);
@@ -339,7 +345,9 @@ int spgemm_predict_batch(const spgemm_batch_plan_t* plan, void* ws, size_t ws_by
  * tile size, blocks per SM), `reps` timed runs each after one untimed run, and
  * writes the fastest (by the median of the runs) to *best and its time in
  * milliseconds to *best_ms (when not NULL).  Synchronous: blocks the host until
- * the measurements are done.  Leaves the workspace prepared with *best (as
+ * the measurements are done.  The phases are tuned in the four-launch form;
+ * the pick is then timed end to end in both forms and the faster kept.
+ * Leaves the workspace prepared with *best (as
  * spgemm_batch_prepare with *best and no staging buffer would) and the plan in
  * *plan.  Outputs are overwritten with the batch's (identical) results. */
 int spgemm_batch_autotune(const spgemm_batch_item_t* items, int32_t n, void* ws, size_t ws_bytes,

@@ -62,11 +62,12 @@ class BatchItemStruct(ctypes.Structure):
 class TuningStruct(ctypes.Structure):
     _fields_ = [("tile_items", ctypes.c_int32), ("warp_table", ctypes.c_int32),
                 ("heavy_threshold", ctypes.c_int32), ("sample_chunk", ctypes.c_int32),
-                ("flop_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("flop_blocks_per_sm", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k in ("tile_items", "warp_table", "heavy_threshold",
-                                               "sample_chunk", "flop_blocks_per_sm")}
+                                               "sample_chunk", "flop_blocks_per_sm", "launches")}
 
 
 class PlanStruct(ctypes.Structure):

@@ -43,6 +43,7 @@ struct DeviceLimits {
   int kb_flop_blocks_per_sm = 0;
   int kb_heavy_dyn_smem = 0;
   int kb_heavy_bitmap_words = 0;
+  int kb_all_blocks_per_sm = 0;
   // single-launch predictor
   int pred_blocks_per_sm = 0;
   int pred_dyn_smem = 0;
@@ -108,6 +109,15 @@ void init_limits(int dev, DeviceLimits* L) {
   }
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kb_flop, kFlopThreads, 0) != cudaSuccess) return;
   L->kb_flop_blocks_per_sm = b;
+  // the batch as one persistent launch: one block per SM
+  const int adyn = (int)kAllDynSmem;
+  if (cudaFuncSetAttribute(kb_all<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, adyn) != cudaSuccess) return;
+  if (cudaFuncSetAttribute(kb_all<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, adyn) != cudaSuccess) return;
+  if (cudaFuncSetAttribute(kb_all<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, adyn) != cudaSuccess) return;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kb_all<512>, kAllThreads, adyn) != cudaSuccess) return;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, kb_all<1024>, kAllThreads, adyn) != cudaSuccess) return;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, kb_all<2048>, kAllThreads, adyn) != cudaSuccess) return;
+  L->kb_all_blocks_per_sm = min(b, min(b2, b3));
   // single-launch predictor: a fixed 128 KB of dynamic shared memory (the rest
   // of the SM's 256 KB stays L1 for the FLOP pass)
   const int pdyn = (int)kPredDynSmem;
@@ -123,7 +133,7 @@ void init_limits(int dev, DeviceLimits* L) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_numeric_rows, kNumThreads, kNumRowsSmem) != cudaSuccess) return;
   L->num_blocks_per_sm = b;
   L->ok = L->pred_blocks_per_sm > 0 && L->num_blocks_per_sm > 0 && L->flop_blocks_per_sm > 0 && L->scan_blocks_per_sm > 0 && L->dedup_blocks_per_sm > 0 &&
-          L->kb_flop_blocks_per_sm > 0 && L->kb_sample_blocks_per_sm[0] > 0 &&
+          L->kb_flop_blocks_per_sm > 0 && L->kb_all_blocks_per_sm > 0 && L->kb_sample_blocks_per_sm[0] > 0 &&
           L->kb_sample_blocks_per_sm[1] > 0 && L->kb_sample_blocks_per_sm[2] > 0;
 }
 
@@ -384,12 +394,14 @@ BatchLayout batch_layout(long long n, long long tiles, long long chunks, long lo
 int resolve_tuning(const spgemm_batch_tuning_t* in, const DeviceLimits* L, spgemm_batch_tuning_t* out) {
   spgemm_batch_tuning_t t{};
   if (in) t = *in;
-  if (t.reserved[0] || t.reserved[1] || t.reserved[2]) return SPGEMM_ERR_INVALID_ARG;
+  if (t.reserved[0] || t.reserved[1]) return SPGEMM_ERR_INVALID_ARG;
   if (t.tile_items == 0) t.tile_items = kDefTile;
   if (t.warp_table == 0) t.warp_table = kDefTable;
   if (t.heavy_threshold == 0) t.heavy_threshold = t.warp_table / 2;
   if (t.sample_chunk == 0) t.sample_chunk = kDefChunk;
   if (t.flop_blocks_per_sm == 0 && L) t.flop_blocks_per_sm = L->kb_flop_blocks_per_sm;
+  if (t.launches == 0) t.launches = 4;
+  if (t.launches != 1 && t.launches != 4) return SPGEMM_ERR_INVALID_ARG;
   if (t.tile_items < kMinTile || t.tile_items > kMaxTile) return SPGEMM_ERR_INVALID_ARG;
   if (t.warp_table != 512 && t.warp_table != 1024 && t.warp_table != 2048) return SPGEMM_ERR_INVALID_ARG;
   if (t.heavy_threshold < 32 || t.heavy_threshold > t.warp_table / 2) return SPGEMM_ERR_INVALID_ARG;
@@ -470,17 +482,46 @@ BatchArgs batch_args(const spgemm_batch_plan_t* plan, void* ws) {
   b.total_chunks = plan->total_chunks;
   b.sample_chunk = plan->tuning.sample_chunk;
   b.heavy_cap = plan->total_candidates;
+  b.total_tab_blocks = plan->total_table_blocks;
   b.heavy_thr = plan->tuning.heavy_threshold;
   return b;
 }
 
-// Queues the batch: counters reset, then the four launches.  ev (optional,
-// 5 events) is recorded before the first launch and after each phase: tables,
-// sampled rows, heavy rows, FLOP.
+// Queues the batch: counters reset, then one cooperative launch of kb_all
+// (tuning.launches = 1) or the four launches.  ev (optional, 5 events) is
+// recorded before the first launch and after each phase: tables, sampled rows,
+// heavy rows, FLOP (with one launch, all four after it).
 int launch_batch(const DeviceLimits* L, const spgemm_batch_plan_t* plan, void* ws, cudaStream_t st,
                  cudaEvent_t* ev) {
   const BatchArgs b = batch_args(plan, ws);
   if (cudaMemsetAsync(b.hdr, 0, kBatchCounterBytes, st) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (plan->tuning.launches == 1) {
+    if (ev) cudaEventRecord(ev[0], st);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)std::min<long long>((long long)L->sms * L->kb_all_blocks_per_sm, kMaxSlots));
+    lc.blockDim = dim3(kAllThreads);
+    lc.dynamicSmemBytes = kAllDynSmem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    const int words = (int)(kAllDynSmem / sizeof(unsigned));
+    prof_mark(false, st);
+    const int wt = plan->tuning.warp_table;
+    const cudaError_t e = wt == 512    ? cudaLaunchKernelEx(&lc, kb_all<512>, b, words)
+                          : wt == 1024 ? cudaLaunchKernelEx(&lc, kb_all<1024>, b, words)
+                                       : cudaLaunchKernelEx(&lc, kb_all<2048>, b, words);
+    prof_mark(true, st);
+    if (ev)
+      for (int i = 1; i < 5; ++i) cudaEventRecord(ev[i], st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return SPGEMM_ERR_CUDA;
+    }
+    return SPGEMM_OK;
+  }
   if (ev) cudaEventRecord(ev[0], st);
   if (plan->total_table_blocks > 0)
     kb_tables<<<(unsigned)plan->total_table_blocks, kTabThreads, 0, st>>>(b);
@@ -929,6 +970,7 @@ int spgemm_batch_autotune(const spgemm_batch_item_t* items, int32_t n, void* ws,
     for (int hi = 0; hi < 2 && !rc; ++hi) {
       for (int ci = 0; ci < 3 && !rc; ++ci) {
         spgemm_batch_tuning_t tu{};
+        tu.launches = 4;  // phases timed apart
         tu.warp_table = tables[ti];
         tu.heavy_threshold = hi == 0 ? tables[ti] / 4 : tables[ti] / 2;
         tu.sample_chunk = chunks[ci];
@@ -960,9 +1002,20 @@ int spgemm_batch_autotune(const spgemm_batch_item_t* items, int32_t n, void* ws,
       }
     }
   }
-  // 3) the pick, end to end; the workspace is left prepared with it
+  // 3) the pick, end to end, in both forms; the faster is kept and the workspace
+  // left prepared with it
   float total = 0.f;
   if (!rc) rc = measure(pick, 0, 4, &total);
+  if (!rc) {
+    spgemm_batch_tuning_t one = pick;
+    one.launches = 1;
+    float t1 = 0.f;
+    if (!(rc = measure(one, 0, 4, &t1)) && t1 < total) {
+      pick = one;
+      total = t1;
+    }
+    if (!rc && pick.launches == 4) rc = measure(pick, 0, 4, &total);  // leave the workspace prepared with the pick
+  }
   for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
   if (rc) return rc;
   *best = pick;

@@ -71,7 +71,9 @@ struct alignas(128) BatchHeader {
   unsigned int tiles_done;        // FLOP tiles finished
   unsigned int big_count;         // rows of more than kBatchBigProducts products queued (from the top)
   unsigned int big_ctr;           // of those, claimed
-  unsigned int pad0[8];
+  unsigned int bar[2];            // grid barriers of the single-launch form (kb_all)
+  unsigned int status;            // SPGEMM_STATUS_* bits of the whole run (a barrier that gave up)
+  unsigned int pad0[5];
   // flag epoch of the last completed run (only grows)
   unsigned int epoch;
   unsigned int pad1[15];
@@ -100,6 +102,7 @@ struct BatchArgs {
   long long total_chunks;
   long long sample_chunk;    // candidates per chunk
   long long heavy_cap;
+  long long total_tab_blocks;  // units of kTabRowsPerBlock B rows (kb_tables blocks)
   int heavy_thr;             // products per row above which a row is queued
 };
 
@@ -125,13 +128,15 @@ __device__ __forceinline__ int warp_last_le(int n, long long x, Key key) {
 // B row-length tables of every case (see k_degree_table), kTabRowsPerBlock
 // rows of one case per block.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTabThreads) kb_tables(BatchArgs b) {
-  const int c = __ldg(b.tab_case + blockIdx.x);
+// Table unit tb (kTabRowsPerBlock rows of one case) by the nthreads threads of a
+// block or group (thread `t` of them).
+__device__ __forceinline__ void batch_table_unit(const BatchArgs& b, long long tb, int t, int nthreads) {
+  const int c = __ldg(b.tab_case + tb);
   const BatchCase& k = b.cases[c];
   const long long K = k.K, nnzB = k.nnzB;
-  const long long r0 = (blockIdx.x - k.tab_blk0) * (long long)kTabRowsPerBlock;
+  const long long r0 = (tb - k.tab_blk0) * (long long)kTabRowsPerBlock;
   bool bad = false;
-  for (long long k0 = r0 + threadIdx.x * 4; k0 < min(K, r0 + kTabRowsPerBlock); k0 += kTabThreads * 4) {
+  for (long long k0 = r0 + t * 4; k0 < min(K, r0 + kTabRowsPerBlock); k0 += (long long)nthreads * 4) {
     unsigned word = 0;
     long long prev = __ldg(k.b_rpt + k0);
 #pragma unroll
@@ -150,6 +155,10 @@ __global__ void __launch_bounds__(kTabThreads) kb_tables(BatchArgs b) {
     *reinterpret_cast<unsigned*>(k.deg8 + k0) = word;
   }
   if (bad) atomicOr(&b.acc[c].status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
+}
+
+__global__ void __launch_bounds__(kTabThreads) kb_tables(BatchArgs b) {
+  batch_table_unit(b, blockIdx.x, threadIdx.x, kTabThreads);
 }
 
 // Fills the per-warp (or per-block) deduplication arguments of case c.
@@ -187,15 +196,30 @@ __device__ __forceinline__ void batch_dedup_args(const BatchArgs& b, int c, Dedu
 // its rows' FLOP / nnz / count to the case's accumulators when it moves on to
 // another case.  TABLE = hash slots per warp (>= 2 * heavy_thr).
 // ---------------------------------------------------------------------------
-template <int TABLE>
-__global__ void __launch_bounds__(kDedupThreads) kb_sample(BatchArgs b) {
-  extern __shared__ int dyn[];
-  __shared__ int list_row[kListCap];
-  __shared__ int list_case[kListCap];
-  __shared__ DedupArgs wa[kDedupWarps];
-  __shared__ int list_n;
-  __shared__ long long s_chunk;
-  __shared__ int s_case;
+// Shared state of the sampled-row pass for a block of NT threads.
+template <int NT>
+struct SampleShared {
+  int list_row[kListCap];
+  int list_case[kListCap];
+  DedupArgs wa[NT / 32];
+  int list_n;
+  long long s_chunk;
+  int s_case;
+};
+
+// The sampled-row pass by a block of NT threads: all of them stage candidates,
+// the first AW warps count the staged rows; dyn holds AW warp tables of TABLE
+// slots.
+template <int TABLE, int NT, int AW = NT / 32>
+__device__ __forceinline__ void batch_sample_phase(const BatchArgs& b, int* dyn, SampleShared<NT>& sh) {
+  static_assert(kListCap > NT, "a staging round fits the list");
+  int* list_row = sh.list_row;
+  int* list_case = sh.list_case;
+  DedupArgs* wa = sh.wa;
+  int& list_n = sh.list_n;
+  long long& s_chunk = sh.s_chunk;
+  int& s_case = sh.s_case;
+  constexpr int NW = NT / 32;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   int* tbl = dyn + warp * TABLE;
   int cur = -1;  // the warp's current case
@@ -259,11 +283,11 @@ __global__ void __launch_bounds__(kDedupThreads) kb_sample(BatchArgs b) {
           list_row[e] = row;
           list_case[e] = cx;
         }
-        base += kDedupThreads;
+        base += NT;
         n += __syncthreads_count(take);
-        if (base >= c_end || n > kListCap - kDedupThreads) break;
+        if (base >= c_end || n > kListCap - NT) break;
       }
-      for (int e = warp; e < n; e += kDedupWarps) {
+      for (int e = warp; warp < AW && e < n; e += AW) {
         const int c = list_case[e], r = list_row[e];
         if (c != cur) {
           flush();
@@ -285,17 +309,33 @@ __global__ void __launch_bounds__(kDedupThreads) kb_sample(BatchArgs b) {
   flush();
 }
 
+template <int TABLE>
+__global__ void __launch_bounds__(kDedupThreads) kb_sample(BatchArgs b) {
+  extern __shared__ int dyn[];
+  __shared__ SampleShared<kDedupThreads> sh;
+  batch_sample_phase<TABLE, kDedupThreads>(b, dyn, sh);
+}
+
 // ---------------------------------------------------------------------------
 // Heavy rows of all cases, one block per row (see heavy_row_nnz): first the
 // rows of more than kBatchBigProducts products (queued from the top of the
 // array), then the others, each claimed one at a time.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kHeavyThreads) kb_heavy(BatchArgs b, int bitmap_words) {
-  extern __shared__ unsigned tab[];
-  __shared__ HeavySmem sm;
-  __shared__ DedupArgs ha;
-  __shared__ long long s_h;
-  __shared__ int s_case;
+struct HeavyShared {
+  HeavySmem sm;
+  DedupArgs ha;
+  long long s_h;
+  int s_case;
+};
+
+// The heavy-row pass by a block of kHeavyThreads threads; tab holds
+// bitmap_words words of shared memory.
+__device__ __forceinline__ void batch_heavy_phase(const BatchArgs& b, unsigned* tab, int bitmap_words,
+                                                  HeavyShared& hs) {
+  HeavySmem& sm = hs.sm;
+  DedupArgs& ha = hs.ha;
+  long long& s_h = hs.s_h;
+  int& s_case = hs.s_case;
   const int t = threadIdx.x;
   const unsigned n_big = (unsigned)min((long long)b.hdr->big_count, b.heavy_cap);
   const unsigned n_heavy = (unsigned)min((long long)b.hdr->heavy_count, b.heavy_cap - n_big);
@@ -330,6 +370,12 @@ __global__ void __launch_bounds__(kHeavyThreads) kb_heavy(BatchArgs b, int bitma
     if (t == 0) atomicAdd(&b.acc[c].z, (unsigned long long)nnz);
     if (__syncthreads_or(bad) && t == 0) atomicOr(&b.acc[c].status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
   }
+}
+
+__global__ void __launch_bounds__(kHeavyThreads) kb_heavy(BatchArgs b, int bitmap_words) {
+  extern __shared__ unsigned tab[];
+  __shared__ HeavyShared hs;
+  batch_heavy_phase(b, tab, bitmap_words, hs);
 }
 
 // ---------------------------------------------------------------------------
@@ -380,10 +426,23 @@ __device__ long long lookback_excl(Slot* slots, int first, int tile, unsigned ep
 // ---------------------------------------------------------------------------
 // FLOP per row, prediction and offsets of all cases, tile by tile.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) kb_flop(BatchArgs b) {
-  __shared__ FlopShared sm;
-  __shared__ FlopArgs fa;
-  __shared__ int s_tile, s_case, s_tile0, s_ntiles;
+template <int NW>
+struct FlopPhaseShared {
+  FlopSharedT<NW> sm;
+  FlopArgs fa;
+  int s_tile, s_case, s_tile0, s_ntiles;
+};
+
+// The FLOP / prediction / offsets pass by a block of NT threads.
+template <int NT>
+__device__ __forceinline__ void batch_flop_phase(const BatchArgs& b, FlopPhaseShared<NT / 32>& fp) {
+  constexpr int NW = NT / 32;
+  FlopSharedT<NW>& sm = fp.sm;
+  FlopArgs& fa = fp.fa;
+  int& s_tile = fp.s_tile;
+  int& s_case = fp.s_case;
+  int& s_tile0 = fp.s_tile0;
+  int& s_ntiles = fp.s_ntiles;
   const int t = threadIdx.x;
   BatchHeader* hdr = b.hdr;
   const unsigned ep = *reinterpret_cast<volatile unsigned*>(&hdr->epoch) + 1u;
@@ -427,7 +486,7 @@ __global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) kb_flop(Bat
 
     bool bad = false;
     long long ftot = 0, ptot = 0;
-    flop_range<kModePredict>(fa, d0, d1, lt > 0, fz, zz, ratio, sm, &sm.out, ftot, ptot, bad);
+    flop_range<kModePredict, NW>(fa, d0, d1, lt > 0, fz, zz, ratio, sm, &sm.out, ftot, ptot, bad);
     if (__syncthreads_or(bad) && t == 0) atomicOr(status, (unsigned)SPGEMM_STATUS_ERR_BAD_INPUT);
     const int i0 = sm.out.i0, i1 = sm.out.i1;
 
@@ -458,8 +517,8 @@ __global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) kb_flop(Bat
       sm.bc[5] = extra_p;
     }
     __syncthreads();
-    const long long blk_f = block_sum<kFlopThreads>(ftot, sm.red) + sm.bc[4];
-    const long long blk_p = block_sum<kFlopThreads>(ptot, sm.red) + sm.bc[5];
+    const long long blk_f = block_sum<NT>(ftot, sm.red) + sm.bc[4];
+    const long long blk_p = block_sum<NT>(ptot, sm.red) + sm.bc[5];
 
     // ---- exclusive prefix of the tile within its case
     if (t < 32) {
@@ -485,7 +544,7 @@ __global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) kb_flop(Bat
     long long run = sm.bc[6];
 
     // ---- offsets of the rows [i0, i1)
-    for (int rb = i0; rb < i1; rb += kFlopThreads * kRowsPerThread) {
+    for (int rb = i0; rb < i1; rb += NT * kRowsPerThread) {
       const int r0 = rb + t * kRowsPerThread;
       int pv[kRowsPerThread];
       long long loc = 0;
@@ -495,7 +554,7 @@ __global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) kb_flop(Bat
         loc += pv[u];
       }
       long long tot;
-      long long ex = block_excl_scan<kFlopThreads>(loc, sm.red, &tot) + run;
+      long long ex = block_excl_scan<NT>(loc, sm.red, &tot) + run;
 #pragma unroll
       for (int u = 0; u < kRowsPerThread; ++u) {
         if (r0 + u < i1) {
@@ -517,6 +576,7 @@ __global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) kb_flop(Bat
         volatile CaseAcc* va = &acc;
         unsigned st = va->status;
         if (va->f == 0) st |= SPGEMM_STATUS_WARN_EMPTY_SAMPLE;
+        st |= *reinterpret_cast<volatile unsigned*>(&hdr->status);  // a grid barrier that gave up
         spgemm_result_t* res = fa.res;
         res->flop_total = (long long)va->F;
         res->flop_s = (long long)va->f;
@@ -539,6 +599,68 @@ __global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) kb_flop(Bat
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(kFlopThreads, SPG_FLOP_MIN_BLOCKS) kb_flop(BatchArgs b) {
+  __shared__ FlopPhaseShared<kFlopWarps> fp;
+  batch_flop_phase<kFlopThreads>(b, fp);
+}
+
+// ---------------------------------------------------------------------------
+// The whole batch as ONE persistent launch: one block of kAllThreads threads
+// per SM (cooperative: every block resident), running the four phases in turn
+// with a grid barrier where a phase needs the previous one complete in every
+// block: the tables and the samples before the heavy rows (the queue is
+// final), the heavy rows before the FLOP pass (every case's f* and z* are
+// final).  Each phase claims its work units as the separate kernels do.  The
+// dynamic shared memory (kAllDynSmem) holds the warp tables of the sampled-row
+// pass (32 warps x TABLE slots), then the heavy rows' bitmap, then the FLOP
+// pass's buffers; it is held to 128 KB so the FLOP pass keeps a large L1.
+// ---------------------------------------------------------------------------
+constexpr int kAllThreads = 1024;
+constexpr size_t kAllDynSmem = 128 * 1024;
+static_assert(kAllThreads == kHeavyThreads, "the heavy rows are counted by the whole block");
+static_assert(sizeof(FlopPhaseShared<kAllThreads / 32>) <= kAllDynSmem, "the FLOP pass's buffers fit");
+
+union AllShared {
+  SampleShared<kAllThreads> sample;
+  HeavyShared heavy;
+};
+
+// Every block arrives at barrier *ctr, then waits (bounded; a wait that gives
+// up sets the run's status) until all G have.
+__device__ __forceinline__ void batch_grid_barrier(unsigned* ctr, unsigned G, unsigned* status) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    count_wait(ctr, G, status);
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <int TABLE>
+__global__ void __launch_bounds__(kAllThreads, 1) kb_all(BatchArgs b, int bitmap_words) {
+  // warps that count sampled rows: as many as the warp tables fit
+  constexpr int kAW = (int)(kAllDynSmem / ((size_t)TABLE * sizeof(int))) < kAllThreads / 32
+                          ? (int)(kAllDynSmem / ((size_t)TABLE * sizeof(int)))
+                          : kAllThreads / 32;
+  static_assert(kAW >= 1, "warp tables fit");
+  extern __shared__ __align__(16) int all_dyn[];
+  __shared__ AllShared ash;
+  const unsigned G = gridDim.x;
+  BatchHeader* hdr = b.hdr;
+  // 1. the B row-length tables (used by the FLOP pass only)
+  for (long long tb = blockIdx.x; tb < b.total_tab_blocks; tb += G) batch_table_unit(b, tb, threadIdx.x, kAllThreads);
+  // 2. the samples and their rows' nnz; heavy rows queued
+  if (b.total_chunks > 0) batch_sample_phase<TABLE, kAllThreads, kAW>(b, all_dyn, ash.sample);
+  batch_grid_barrier(&hdr->bar[0], G, &hdr->status);
+  // 3. the heavy rows
+  batch_heavy_phase(b, reinterpret_cast<unsigned*>(all_dyn), bitmap_words, ash.heavy);
+  batch_grid_barrier(&hdr->bar[1], G, &hdr->status);
+  // 4. FLOP per row, prediction and offsets
+  batch_flop_phase<kAllThreads>(b, *reinterpret_cast<FlopPhaseShared<kAllThreads / 32>*>(all_dyn));
 }
 
 }  // namespace spg

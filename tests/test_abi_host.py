@@ -177,6 +177,8 @@ def test_batch_host_errors(lib):
     t = sp.tuning()
     t.reserved[1] = 1
     assert _prepare(lib, good, 2, t, plan, ws, None, None) == sp.ERR_INVALID_ARG
+    for bad_launches in (dict(launches=2), dict(launches=3)):
+        assert _prepare(lib, good, 2, sp.tuning(**bad_launches), plan, ws, None, None) == sp.ERR_INVALID_ARG
     nopred = _items(lib, shapes[:1])
     nopred[0].pred_row = None
     assert _prepare(lib, nopred, 1, None, plan, ws, None, bad) == sp.ERR_INVALID_ARG

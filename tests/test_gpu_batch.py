@@ -139,11 +139,15 @@ def test_batch_split_rows_match_oracle():
 
 
 TUNINGS = [
-    dict(),
+    dict(),  # four launches
+    dict(launches=1),
     dict(tile_items=4096, sample_chunk=4096),
+    dict(tile_items=4096, sample_chunk=4096, launches=4),
     dict(warp_table=512, heavy_threshold=32, tile_items=65536),
+    dict(warp_table=512, heavy_threshold=32, tile_items=65536, launches=4),
     dict(warp_table=2048, heavy_threshold=1024, sample_chunk=131072, tile_items=8192),
-    dict(warp_table=1024, heavy_threshold=64, flop_blocks_per_sm=1),
+    dict(warp_table=2048, heavy_threshold=1024, sample_chunk=131072, tile_items=8192, launches=4),
+    dict(warp_table=1024, heavy_threshold=64, flop_blocks_per_sm=1, launches=4),
 ]
 
 
@@ -165,9 +169,11 @@ def test_tuning_never_changes_results():
                 assert a[k] == b[k], (k, i, tu)
 
 
-def test_repeated_runs_and_graph_replay():
+@pytest.mark.parametrize("launches", [1, 4])
+def test_repeated_runs_and_graph_replay(launches):
     cases = _edge_cases()
-    batch = sp.Batch(_device_cases(cases), want_flop=True)
+    batch = sp.Batch(_device_cases(cases), want_flop=True, tuning_=sp.tuning(launches=launches))
+    assert batch.plan.tuning.launches == launches
     batch.run()
     first = _batch_outputs(batch)
     for _ in range(3):
@@ -240,6 +246,7 @@ def test_autotune_picks_a_valid_tuning_with_identical_results(small_family):
     t = best.as_dict()
     assert t["warp_table"] in (512, 1024, 2048) and 32 <= t["heavy_threshold"] <= t["warp_table"] // 2
     assert 4096 <= t["tile_items"] and t["sample_chunk"] % 256 == 0 and t["flop_blocks_per_sm"] >= 1
+    assert t["launches"] in (1, 4)
     assert batch.plan.tuning.as_dict() == t
     for p in batch.outputs:
         p[0].fill_(-1)
@@ -263,3 +270,23 @@ def test_batch_with_full_size_cases_matches_oracle():
     for c, g in zip(cases, _batch_outputs(batch)):
         o = oracle_predict(c["A"], c["B"], c["mode"], c["seed"], c["threshold"], c["sample_num"])
         assert_prediction_equal(g, o, c["name"])
+
+
+def test_one_launch_and_four_launches_agree_on_full_size_cases():
+    # the single persistent launch (grid barriers between the phases) and the
+    # four launches give the same integers on large, uneven cases
+    cases = []
+    for st, n, v in (("rmat", 1 << 18, 20), ("er", 1 << 18, 3), ("st27", 1 << 16, 9), ("lap2d", 1 << 12, 1)):
+        A, B, name = W.family_case(st, n, v)
+        cases.append(dict(_case(A, B, seed=v), name=name))
+    dev = _device_cases(cases)
+    outs = []
+    for launches in (1, 4):
+        batch = sp.Batch(dev, want_flop=True, tuning_=sp.tuning(launches=launches))
+        batch.run()
+        outs.append(_batch_outputs(batch))
+    for c, a, b in zip(cases, *outs):
+        for k in ("pred", "offsets", "flop"):
+            np.testing.assert_array_equal(a[k], b[k], err_msg=f"{k} {c['name']}")
+        assert {k: a[k] for k in a if k not in ("pred", "offsets", "flop")} == \
+               {k: b[k] for k in b if k not in ("pred", "offsets", "flop")}, c["name"]
