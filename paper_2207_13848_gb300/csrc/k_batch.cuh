@@ -66,14 +66,13 @@ struct alignas(128) BatchHeader {
   // work counters, zeroed before every run
   unsigned long long sample_ctr;  // candidate chunks claimed
   unsigned int heavy_count;       // rows queued for kb_heavy
-  unsigned int heavy_ctr;         // queued rows claimed
+  unsigned int heavy_ctr;         // queued rows claimed (the big rows' queue first, then the other)
   unsigned int tile_ctr;          // FLOP tiles claimed
   unsigned int tiles_done;        // FLOP tiles finished
   unsigned int big_count;         // rows of more than kBatchBigProducts products queued (from the top)
-  unsigned int big_ctr;           // of those, claimed
   unsigned int bar[2];            // grid barriers of the single-launch form (kb_all)
   unsigned int status;            // SPGEMM_STATUS_* bits of the whole run (a barrier that gave up)
-  unsigned int pad0[5];
+  unsigned int pad0[6];
   // flag epoch of the last completed run (only grows)
   unsigned int epoch;
   unsigned int pad1[15];
@@ -219,7 +218,6 @@ __device__ __forceinline__ void batch_sample_phase(const BatchArgs& b, int* dyn,
   int& list_n = sh.list_n;
   long long& s_chunk = sh.s_chunk;
   int& s_case = sh.s_case;
-  constexpr int NW = NT / 32;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   int* tbl = dyn + warp * TABLE;
   int cur = -1;  // the warp's current case
@@ -319,13 +317,18 @@ __global__ void __launch_bounds__(kDedupThreads) kb_sample(BatchArgs b) {
 // ---------------------------------------------------------------------------
 // Heavy rows of all cases, one block per row (see heavy_row_nnz): first the
 // rows of more than kBatchBigProducts products (queued from the top of the
-// array), then the others, each claimed one at a time.
+// array), then the others, each claimed one at a time.  A block claims its
+// next row when it starts one (the claim's round trip is hidden behind the
+// row), and finds a row's case among the cases' first rows, held in shared
+// memory for batches of at most kCaseCache cases.
 // ---------------------------------------------------------------------------
+constexpr int kCaseCache = 1024;
 struct HeavyShared {
   HeavySmem sm;
   DedupArgs ha;
   long long s_h;
   int s_case;
+  int row_base[kCaseCache];  // cases' first batch-wide rows (total rows < 2^31)
 };
 
 // The heavy-row pass by a block of kHeavyThreads threads; tab holds
@@ -339,24 +342,30 @@ __device__ __forceinline__ void batch_heavy_phase(const BatchArgs& b, unsigned* 
   const int t = threadIdx.x;
   const unsigned n_big = (unsigned)min((long long)b.hdr->big_count, b.heavy_cap);
   const unsigned n_heavy = (unsigned)min((long long)b.hdr->heavy_count, b.heavy_cap - n_big);
+  const bool cached = b.n_cases <= kCaseCache;
+  if (cached)
+    for (int i = t; i < b.n_cases; i += kHeavyThreads) hs.row_base[i] = (int)b.cases[i].row_base;
+  unsigned q_next = 0;  // thread 0: the claim in flight
+  if (t == 0) q_next = atomicAdd(&b.hdr->heavy_ctr, 1u);
   for (;;) {
     if (t == 0) {
+      const unsigned q = q_next;
       long long h = -1;
-      const unsigned q = atomicAdd(&b.hdr->big_ctr, 1u);
       if (q < n_big) {
         h = b.heavy_cap - 1 - q;
-      } else {
-        const unsigned r = atomicAdd(&b.hdr->heavy_ctr, 1u);
-        if (r < n_heavy) h = r;
+      } else if (q - n_big < n_heavy) {
+        h = q - n_big;
       }
       s_h = h;
+      if (h >= 0) q_next = atomicAdd(&b.hdr->heavy_ctr, 1u);  // the next row, claimed during this one
     }
-    __syncthreads();
+    __syncthreads();  // (also orders the case cache)
     const long long h = s_h;
     if (h < 0) break;
     const int g = b.heavy[h] - 1;
     if (t < 32) {
-      const int c = warp_last_le(b.n_cases, (long long)g, [&](int i) { return b.cases[i].row_base; });
+      const int c = cached ? warp_last_le(b.n_cases, (long long)g, [&](int i) { return (long long)hs.row_base[i]; })
+                           : warp_last_le(b.n_cases, (long long)g, [&](int i) { return b.cases[i].row_base; });
       if (t == 0) {
         s_case = c;
         batch_dedup_args(b, c, ha);

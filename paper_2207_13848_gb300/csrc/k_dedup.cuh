@@ -361,22 +361,26 @@ __device__ __forceinline__ long long heavy_products(const DedupArgs& a, const He
   return cnt;
 }
 
+// preloaded: the row is one group whose offsets heavy_row_flop left in sm.
 template <bool BITMAP, bool COUNT = true>
 __device__ long long heavy_count_pass(const DedupArgs& a, long long rb, long long re, HeavySmem& sm,
                                       unsigned* tab, int lg_or_words, long long lo, long long hi,
-                                      bool& bad) {
+                                      bool& bad, bool preloaded = false) {
   const int t = threadIdx.x, warp = t >> 5;
   long long cnt = 0;
   for (long long g = rb; g < re; g += kHeavyThreads) {
-    long long s = 0, len = 0;
-    if (g + t < re) b_row(a, __ldg(a.a_col + g + t), s, len, bad);
-    long long T;
-    const long long excl = block_excl_scan<kHeavyThreads>(len, sm.red, &T);
-    sm.ex[t] = excl;
-    sm.bs[t] = s - excl;
     const int nent = (int)min((long long)kHeavyThreads, re - g);
-    if (t == 0) sm.ex[nent] = T;
-    __syncthreads();
+    if (!preloaded) {
+      long long s = 0, len = 0;
+      if (g + t < re) b_row(a, __ldg(a.a_col + g + t), s, len, bad);
+      long long Tg;
+      const long long excl = block_excl_scan<kHeavyThreads>(len, sm.red, &Tg);
+      sm.ex[t] = excl;
+      sm.bs[t] = s - excl;
+      if (t == 0) sm.ex[nent] = Tg;
+      __syncthreads();
+    }
+    const long long T = sm.ex[nent];
     // warp w takes products [w*Q, (w+1)*Q), Q a multiple of 32
     const long long Q = ((T + 32 * 32 - 1) / (32 * 32)) * 32;
     const long long p_beg = (long long)warp * Q, p_end = min(T, p_beg + Q);
@@ -398,32 +402,50 @@ __device__ long long heavy_count_pass(const DedupArgs& a, long long rb, long lon
 // Exact nnz of one heavy row by the whole block (kHeavyThreads threads): a
 // shared hash table when the row has at most kBlockHashCap products, else a
 // bitmap over B's columns, one column range of bitmap_words * 32 at a time.
-// The row's A entry range [*rb, *re) and its FLOP, by the whole block.
+// The row's A entry range [*rb, *re) and its FLOP, by the whole block.  With
+// `preloaded` given, a row of at most kHeavyThreads entries leaves its
+// entries' product offsets and B row starts in sm (*preloaded = true) for the
+// counting pass, which then reads no row bounds again; they are visible to
+// every thread after the caller's next __syncthreads.
 __device__ long long heavy_row_flop(const DedupArgs& a, int row, HeavySmem& sm, long long* rb_out,
-                                    long long* re_out, bool& bad) {
+                                    long long* re_out, bool& bad, bool* preloaded = nullptr) {
   long long rb = __ldg(a.a_rpt + row), re = __ldg(a.a_rpt + row + 1);
   if (!clamp_range(rb, re, a.nnzA)) bad = true;
+  *rb_out = rb;
+  *re_out = re;
+  if (preloaded) *preloaded = false;
+  if (preloaded && re - rb <= kHeavyThreads) {
+    const int t = threadIdx.x;
+    long long s = 0, len = 0;
+    if (rb + t < re) b_row(a, __ldg(a.a_col + rb + t), s, len, bad);
+    long long T;
+    const long long excl = block_excl_scan<kHeavyThreads>(len, sm.red, &T);
+    sm.ex[t] = excl;
+    sm.bs[t] = s - excl;
+    if (t == 0) sm.ex[re - rb] = T;
+    *preloaded = true;
+    return T;
+  }
   long long fl = 0;
   for (long long j = rb + threadIdx.x; j < re; j += kHeavyThreads) {
     long long s, len;
     b_row(a, __ldg(a.a_col + j), s, len, bad);
     fl += len;
   }
-  *rb_out = rb;
-  *re_out = re;
   return block_sum<kHeavyThreads>(fl, sm.red);
 }
 
 // Exact nnz of the row whose entries are [rb, re) and FLOP is flop, by the
-// whole block (see heavy_row_nnz).
+// whole block (see heavy_row_nnz); preloaded as heavy_row_flop set it.
 __device__ long long heavy_row_count(const DedupArgs& a, long long rb, long long re, long long flop,
-                                     HeavySmem& sm, unsigned* tab, int bitmap_words, bool& bad) {
+                                     HeavySmem& sm, unsigned* tab, int bitmap_words, bool& bad,
+                                     bool preloaded = false) {
   long long nnz = 0;
   if (flop <= kBlockHashCap) {
     const int lg = ceil_log2((uint32_t)(2 * flop));
     for (int i = threadIdx.x; i < (1 << lg); i += kHeavyThreads) tab[i] = 0xffffffffu;
     __syncthreads();
-    nnz = heavy_count_pass<false>(a, rb, re, sm, tab, lg, 0, 0, bad);
+    nnz = heavy_count_pass<false>(a, rb, re, sm, tab, lg, 0, 0, bad, preloaded);
   } else {
     const long long range = (long long)bitmap_words * 32;
     for (long long lo = 0; lo < a.N; lo += range) {
@@ -431,7 +453,7 @@ __device__ long long heavy_row_count(const DedupArgs& a, long long rb, long long
       const int words = (int)((hi - lo + 31) / 32);
       for (int i = threadIdx.x; i < words; i += kHeavyThreads) tab[i] = 0u;
       __syncthreads();
-      nnz += heavy_count_pass<true>(a, rb, re, sm, tab, words, lo, hi, bad);
+      nnz += heavy_count_pass<true>(a, rb, re, sm, tab, words, lo, hi, bad, preloaded);
     }
   }
   return nnz;
@@ -440,9 +462,10 @@ __device__ long long heavy_row_count(const DedupArgs& a, long long rb, long long
 __device__ long long heavy_row_nnz(const DedupArgs& a, int row, HeavySmem& sm, unsigned* tab,
                                    int bitmap_words, bool& bad, long long* flop_out = nullptr) {
   long long rb, re;
-  const long long flop = heavy_row_flop(a, row, sm, &rb, &re, bad);
+  bool pre;
+  const long long flop = heavy_row_flop(a, row, sm, &rb, &re, bad, &pre);
   if (flop_out) *flop_out = flop;
-  return heavy_row_count(a, rb, re, flop, sm, tab, bitmap_words, bad);
+  return heavy_row_count(a, rb, re, flop, sm, tab, bitmap_words, bad, pre);
 }
 
 __global__ void __launch_bounds__(kHeavyThreads) k_dedup_heavy(DedupArgs a, int bitmap_words) {

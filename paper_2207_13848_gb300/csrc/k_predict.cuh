@@ -392,13 +392,19 @@ __device__ void sample_per_warp(const DedupArgs& d, int* tables, int* list, long
 // Thread 0: claims the next heavy-queue entry and returns it (see push_heavy),
 // or 0 once every queued row is taken (the queue is final when every block's
 // sampling group has finished).  Waits for an entry whose writer has not
-// stored it yet.
-__device__ int claim_heavy_row(WsHeader* hdr, int* heavy, unsigned long long cap, unsigned G) {
-  // nothing to take once every sampling group is done and every queued entry
-  // has been claimed (one round trip instead of a claim and its checks)
-  if (flag_load(&hdr->sample_done) >= G) {
-    volatile WsHeader* vh = hdr;
-    if ((unsigned long long)vh->heavy_ctr >= min((unsigned long long)vh->heavy_count, cap)) return 0;
+// stored it yet.  ctr_hint and cnt_hint are earlier unordered reads of
+// heavy_ctr and heavy_count: both only grow during a launch, so an index below
+// cnt_hint names an entry that exists, and "nothing left" is concluded only
+// from the ordered reads below.
+__device__ int claim_heavy_row(WsHeader* hdr, int* heavy, unsigned long long cap, unsigned G, unsigned ctr_hint,
+                               unsigned cnt_hint) {
+  if ((unsigned long long)ctr_hint >= min((unsigned long long)cnt_hint, cap)) {
+    // maybe nothing to take: every sampling group done and every queued entry
+    // claimed (one round trip instead of a claim and its checks)
+    if (flag_load(&hdr->sample_done) >= G) {
+      volatile WsHeader* vh = hdr;
+      if ((unsigned long long)vh->heavy_ctr >= min((unsigned long long)vh->heavy_count, cap)) return 0;
+    }
   }
   const unsigned h = atomicAdd(&hdr->heavy_ctr, 1u);
   const uint64_t t0 = global_ns();
@@ -407,7 +413,7 @@ __device__ int claim_heavy_row(WsHeader* hdr, int* heavy, unsigned long long cap
     // only entries below the count queued so far exist (a clean workspace may
     // hold anything past them); an existing entry reads 0 until its writer's
     // store lands
-    if (h < cap && h < flag_load(&hdr->heavy_count)) {
+    if (h < cap && (h < cnt_hint || h < flag_load(&hdr->heavy_count))) {
       const unsigned v = flag_load(reinterpret_cast<const unsigned*>(heavy + h));
       if (v != 0) {
         heavy[h] = 0;  // taken
@@ -431,19 +437,47 @@ constexpr long long kHugeProducts = 1ll << 20;  // sampled rows with more produc
 constexpr long long kPartProducts = 1ll << 17;  // products per part, at least
 constexpr unsigned kPartParked = 0xffff0000u;   // part_ctr while a slot is being set up
 
-// Thread 0: claims a part of a split row; returns slot * 128 + part, or -1.
-__device__ int claim_part(HugeSlot* hs) {
-  for (int s = 0; s < kHugeSlots; ++s) {
-    if (flag_load(&hs[s].state) != 2u) continue;
-    volatile HugeSlot* v = hs + s;
-    if (v->part_ctr >= v->parts) continue;
-    const unsigned q = atomicAdd(&hs[s].part_ctr, 1u);
-    __threadfence();
-    // the slot may have been finished and set up again in between: the claim
-    // counts only against the row now published there
-    if (flag_load(&hs[s].state) == 2u && q < v->parts) return s * 128 + (int)q;
+// Warp 0: the block's next heavy work.  *part = slot * 128 + part for a part
+// of a split row (-1 if none is open), else *enc = a queued row's entry (0 once
+// every queued row is taken).  One round of loads, all in flight together,
+// reads the split slots (one lane each) and the queue counters; a claimed
+// part counts only if its slot still holds the row it was read for.
+__device__ void claim_heavy_work(WsHeader* hdr, HugeSlot* hs, int* heavy, unsigned long long cap, unsigned G,
+                                 int* part_out, int* enc_out) {
+  const int lane = threadIdx.x & 31;
+  bool open = false;
+  unsigned hint = 0;
+  if (hs && lane < kHugeSlots) {
+    volatile HugeSlot* v = hs + lane;
+    const unsigned st = v->state, pc = v->part_ctr, np = v->parts;
+    open = st == 2u && pc < np;
+  } else if (lane == kHugeSlots) {
+    hint = reinterpret_cast<volatile WsHeader*>(hdr)->heavy_ctr;
+  } else if (lane == kHugeSlots + 1) {
+    hint = reinterpret_cast<volatile WsHeader*>(hdr)->heavy_count;
   }
-  return -1;
+  const unsigned ctr_hint = __shfl_sync(kFull, hint, kHugeSlots);
+  const unsigned cnt_hint = __shfl_sync(kFull, hint, kHugeSlots + 1);
+  unsigned m = __ballot_sync(kFull, open);
+  int part = -1;
+  while (m != 0 && part < 0) {
+    const int s = __ffs(m) - 1;
+    m &= m - 1;
+    if (lane == 0) {
+      const unsigned q = atomicAdd(&hs[s].part_ctr, 1u);
+      __threadfence();
+      // the slot may have been finished and set up again in between: the claim
+      // counts only against the row now published there
+      volatile HugeSlot* v = hs + s;
+      if (flag_load(&hs[s].state) == 2u && q < v->parts) part = s * 128 + (int)q;
+    }
+    part = __shfl_sync(kFull, part, 0);
+  }
+  if (lane == 0) {
+    *part_out = part;
+    *enc_out = part >= 0 ? 0 : claim_heavy_row(hdr, heavy, cap, G, ctr_hint, cnt_hint);
+  }
+  __syncwarp();
 }
 
 // The whole block: sets up slot h for a row with entries [rb, re) and FLOP
@@ -502,10 +536,7 @@ __device__ __noinline__ bool heavy_phase(const PredArgs& p, PredStatic& ss, unsi
   uint64_t t_start = global_ns();
   unsigned seen_done = 0;
   for (;;) {
-    if (t == 0) {
-      ss.s_part = hs ? claim_part(hs) : -1;
-      ss.s_enc = ss.s_part >= 0 ? 0 : claim_heavy_row(hdr, d.heavy, (unsigned long long)d.heavy_cap, (unsigned)G);
-    }
+    if (t < 32) claim_heavy_work(hdr, hs, d.heavy, (unsigned long long)d.heavy_cap, (unsigned)G, &ss.s_part, &ss.s_enc);
     __syncthreads();
     const int part = ss.s_part, enc = ss.s_enc;
     if ((part >= 0 || enc != 0) && flop_in_smem) {  // the tables below overwrite sflop: move it out first
@@ -564,7 +595,8 @@ __device__ __noinline__ bool heavy_phase(const PredArgs& p, PredStatic& ss, unsi
       // ---- a queued row: counted here, or split for all blocks
       long long rb, re;
       const int row = enc > 0 ? enc - 1 : -enc - 1;
-      const long long flop = heavy_row_flop(d, row, ss.heavy, &rb, &re, bad);
+      bool pre;
+      const long long flop = heavy_row_flop(d, row, ss.heavy, &rb, &re, bad, &pre);
       if (t == 0) {
         if (enc < 0) atomicAdd(&hdr->f_acc, (unsigned long long)flop);
         ss.s_part = -1;
@@ -583,7 +615,7 @@ __device__ __noinline__ bool heavy_phase(const PredArgs& p, PredStatic& ss, unsi
       if (ss.s_part >= 0) {
         split_row(d, hs + ss.s_part, rb, re, flop, ss.red, bad);
       } else {  // small enough, or every split slot is taken: counted here
-        const long long nnz = heavy_row_count(d, rb, re, flop, ss.heavy, tab, p.bitmap_words, bad);
+        const long long nnz = heavy_row_count(d, rb, re, flop, ss.heavy, tab, p.bitmap_words, bad, pre);
         if (t == 0) {
           atomicAdd(&hdr->z_acc, (unsigned long long)nnz);
           __threadfence();
