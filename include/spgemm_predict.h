@@ -290,7 +290,7 @@ typedef struct spgemm_batch_tuning {
                                  grid barriers between the phases); 4: one persistent launch per
                                  phase (tables, sampled rows, heavy rows, FLOP and offsets), each
                                  with its own shared-memory size and block shape; default 4, the
-                                 faster at scale (625 family cases: 34.8 against 43.9 ms) */
+                                 faster at scale (625 family cases: 33.3 against 42.0 ms) */
   int32_t reserved[2];        /* must be 0 */
 } spgemm_batch_tuning_t;
 
