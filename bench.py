@@ -945,7 +945,7 @@ def main(argv=None):
     ap.add_argument("--batch-sizes", type=int, nargs="+", default=[12, 14, 16, 18, 20],
                     help="log2 of the family's sizes for --suite batch (default: all five, 625 cases)")
     ap.add_argument("--serve-requests", type=int, default=10000)
-    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--serve-batch-rows", type=int, default=1 << 18,
                     help="requests with at most this many rows are merged into batched launches")
     ap.add_argument("--serve-max-batch", type=int, default=128)

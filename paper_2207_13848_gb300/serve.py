@@ -108,7 +108,7 @@ class Server:
     with A.rows <= batch_rows that wait together are merged into one batched
     launch of at most max_batch cases (batch_rows = 0: never merge)."""
 
-    def __init__(self, slots=8, memory_budget=8 << 30, device="cuda", batch_rows=1 << 18, max_batch=128,
+    def __init__(self, slots=3, memory_budget=8 << 30, device="cuda", batch_rows=1 << 18, max_batch=128,
                  streams=1):
         torch = _torch()
         if slots < 1:
@@ -470,10 +470,16 @@ def latency_summary(requests):
             "mean": float(lat.mean()), "span": float(span), "n": len(requests)}
 
 
-def run_poisson(server, pool, rate, n_requests, seed=0, ratio=0.01):
+def run_poisson(server, pool, rate, n_requests, seed=0, ratio=0.01, pause_gc=True):
     """Offer n_requests predictions with Poisson arrivals at `rate` per second,
     each on an operand pair drawn uniformly from `pool` (a list of (A, B) device
-    pairs) with its own sampling seed; returns the finished requests in id order."""
+    pairs) with its own sampling seed; returns the finished requests in id order.
+    pause_gc: Python's cyclic garbage collector is off while the requests are
+    served (and back on afterwards).  The loop's objects hold no reference
+    cycles, so reference counting frees them, and a full collection over the
+    run's tens of thousands of live objects would stall the host loop, and with
+    it every request waiting or arriving meanwhile, for tens of milliseconds."""
+    import gc
     import numpy as np
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, size=n_requests) if rate > 0 else np.zeros(n_requests)
@@ -481,13 +487,20 @@ def run_poisson(server, pool, rate, n_requests, seed=0, ratio=0.01):
     picks = rng.integers(0, len(pool), size=n_requests)
     T = int(ratio * (1 << 32))
     server.finished = []
-    t0 = time.perf_counter()
-    i = 0
-    while i < n_requests or server.wait_small or server.wait_large or server.inflight:
-        now = time.perf_counter() - t0
-        while i < n_requests and arrivals[i] <= now:
-            A, B = pool[picks[i]]
-            server.submit(A, B, config(threshold=T, seed=int(i)), arrival=t0 + arrivals[i], index=int(i))
-            i += 1
-        server.poll()
+    gc_on = gc.isenabled()
+    if pause_gc:
+        gc.disable()
+    try:
+        t0 = time.perf_counter()
+        i = 0
+        while i < n_requests or server.wait_small or server.wait_large or server.inflight:
+            now = time.perf_counter() - t0
+            while i < n_requests and arrivals[i] <= now:
+                A, B = pool[picks[i]]
+                server.submit(A, B, config(threshold=T, seed=int(i)), arrival=t0 + arrivals[i], index=int(i))
+                i += 1
+            server.poll()
+    finally:
+        if pause_gc and gc_on:
+            gc.enable()
     return sorted(server.finished, key=lambda r: r.index), picks
