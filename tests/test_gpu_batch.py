@@ -290,3 +290,32 @@ def test_one_launch_and_four_launches_agree_on_full_size_cases():
             np.testing.assert_array_equal(a[k], b[k], err_msg=f"{k} {c['name']}")
         assert {k: a[k] for k in a if k not in ("pred", "offsets", "flop")} == \
                {k: b[k] for k in b if k not in ("pred", "offsets", "flop")}, c["name"]
+
+
+@pytest.mark.parametrize("launches", [1, 4])
+def test_batch_of_more_cases_than_the_case_cache(launches):
+    # above 1024 cases the heavy pass finds a queued row's case by a search in
+    # global memory instead of the shared-memory copy of the cases' first rows:
+    # 1100 small cases, with hub rows (queued as heavy) in cases on both sides
+    # of case 1024, each compared with the oracle
+    rng = np.random.default_rng(1100)
+    hosts = []
+    for i in range(1100):
+        if i % 97 == 5 or i in (1023, 1024, 1099):
+            # hub rows of ~2400 products; every row sampled, so both are queued
+            A, B = wide_hubs(300, 200, 900, 2, 60, 40, seed=i)
+            hosts.append(_case(A, B, seed=i, threshold=TWO32))
+        else:
+            A = W.erdos_renyi(int(rng.integers(1, 120)), 4, 5000 + i)
+            hosts.append(_case(A, A, ratio=0.5, seed=i))
+    dev = _device_cases(hosts)
+    batch = sp.Batch(dev, want_flop=True, tuning_=sp.tuning(launches=launches))
+    batch.run()
+    got = _batch_outputs(batch)
+    hub_cases = [i for i in range(1100) if i % 97 == 5 or i in (1023, 1024, 1099)]
+    for i in range(1100):
+        c = hosts[i]
+        if i not in hub_cases and i % 37:
+            continue  # every hub case, and a sample of the others
+        o = oracle_predict(c["A"], c["B"], c["mode"], c["seed"], c["threshold"])
+        assert_prediction_equal(got[i], o, f"case {i}")
