@@ -109,12 +109,29 @@ __device__ __forceinline__ int num_slot(int* keys, int lg, int key) {
   return -1;
 }
 
-// Room for row `row` in its share of the allocation: alloc[row+1] - alloc[row],
-// cut to what the arrays hold (alloc_cap entries).
-__device__ __forceinline__ long long num_alloc_room(const NumArgs& a, int row) {
-  const long long d = a.alloc[row], cap = a.alloc[row + 1] - d;
+// Room for a row whose share of the allocation is [d, d1), cut to what the
+// arrays hold (alloc_cap entries).
+__device__ __forceinline__ long long num_alloc_room(const NumArgs& a, long long d, long long d1) {
+  const long long cap = d1 - d;
   if (d < 0 || cap <= 0 || d >= a.alloc_cap) return 0;
   return min(cap, a.alloc_cap - d);
+}
+
+// A row's own bounds in its target when it has them before its size is known
+// (its share of the allocation, or its exact offsets); none in pool mode.
+// Read when the row starts, so that the round trip overlaps the row's work.
+struct NumBounds {
+  long long lo, hi;
+  bool have;
+};
+__device__ __forceinline__ NumBounds num_bounds(const NumArgs& a, int row) {
+  NumBounds b{0, 0, false};
+  if (a.mode != kNumInto) {
+    b = NumBounds{a.out_rpt[row], a.out_rpt[row + 1], true};
+  } else if (a.alloc) {
+    b = NumBounds{a.alloc[row], a.alloc[row + 1], true};
+  }
+  return b;
 }
 
 // Pool mode: n entries from a stripe of the pool (the row's stripe first);
@@ -146,15 +163,16 @@ struct NumTarget {
   long long limit;  // the target arrays' length: nothing is written at or past it
 };
 
-__device__ NumTarget num_target(const NumArgs& a, int row, long long n) {
+__device__ NumTarget num_target(const NumArgs& a, int row, long long n, const NumBounds* pre = nullptr) {
   NumTarget t;
+  const NumBounds b = pre && pre->have ? *pre : num_bounds(a, row);
   if (a.mode == kNumInto) {
     t.col = a.c_col;
     t.val = a.c_val;
     t.limit = a.alloc_cap;
     if (a.alloc) {
-      t.dst = a.alloc[row];
-      t.cap = num_alloc_room(a, row);
+      t.dst = b.lo;
+      t.cap = num_alloc_room(a, b.lo, b.hi);
     } else {
       t.dst = num_pool_take(a, row, n);
       t.cap = t.dst >= 0 ? n : 0;
@@ -163,8 +181,8 @@ __device__ NumTarget num_target(const NumArgs& a, int row, long long n) {
     a.row_start[row] = fits ? t.dst : -1;
     if (!fits) t.cap = 0;
   } else {
-    t.dst = a.out_rpt[row];
-    t.cap = a.out_rpt[row + 1] - t.dst;
+    t.dst = b.lo;
+    t.cap = b.hi - b.lo;
     t.col = a.out_col;
     t.val = a.out_val;
     t.limit = a.out_cap;
@@ -196,12 +214,22 @@ __device__ __forceinline__ void num_queue(const NumArgs& a, int row) {
 // row has more than kNumWarpCap products and was queued for a block.
 __device__ long long num_row_warp(const NumArgs& a, int row, int* keys, float* vals, bool& bad) {
   const int lane = threadIdx.x & 31;
+  NumBounds pre{0, 0, false};
+  if (lane == 0) pre = num_bounds(a, row);
   long long rb = __ldg(a.a_rpt + row), re = __ldg(a.a_rpt + row + 1);
   if (!clamp_range(rb, re, a.nnzA)) bad = true;
-  long long flop = 0;
+  // the FLOP of the row; the first 32 entries' B rows and values stay in
+  // registers for the products loop
+  long long flop = 0, s0 = 0, len0 = 0;
+  float av0 = 0.0f;
   for (long long j = rb + lane; j < re; j += 32) {
     long long s, len;
     num_b_row(a, __ldg(a.a_col + j), s, len, bad);
+    if (j - rb < 32) {
+      s0 = s;
+      len0 = len;
+      av0 = __ldg(a.a_val + j);
+    }
     flop += len;
   }
   flop = warp_sum(flop);
@@ -218,11 +246,16 @@ __device__ long long num_row_warp(const NumArgs& a, int row, int* keys, float* v
   __syncwarp();
   // products, 32 entries of A at a time: lane p of a step takes product p
   for (long long g = rb; g < re; g += 32) {
-    long long s = 0, len = 0;
-    float av = 0.0f;
-    if (g + lane < re) {
-      num_b_row(a, __ldg(a.a_col + g + lane), s, len, bad);
-      av = __ldg(a.a_val + g + lane);
+    long long s = s0, len = len0;
+    float av = av0;
+    if (g != rb) {
+      s = 0;
+      len = 0;
+      av = 0.0f;
+      if (g + lane < re) {
+        num_b_row(a, __ldg(a.a_col + g + lane), s, len, bad);
+        av = __ldg(a.a_val + g + lane);
+      }
     }
     const int ilen = (int)len;
     const int inc = warp_incl_scan(ilen);
@@ -269,7 +302,7 @@ __device__ long long num_row_warp(const NumArgs& a, int row, int* keys, float* v
   int nnz = 0;
   for (int i0 = 0; i0 < P; i0 += 32) nnz += __popc(__ballot_sync(kFull, keys[i0 + lane] != -1));
   NumTarget t{};
-  if (lane == 0) t = num_target(a, row, nnz);
+  if (lane == 0) t = num_target(a, row, nnz, &pre);
   t.dst = __shfl_sync(kFull, t.dst, 0);
   t.cap = __shfl_sync(kFull, t.cap, 0);
   t.limit = __shfl_sync(kFull, t.limit, 0);
