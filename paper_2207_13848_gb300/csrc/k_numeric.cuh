@@ -32,7 +32,7 @@
 
 namespace spg {
 
-constexpr int kNumThreads = 256;                   // warp-per-row pass: 8 warps per block
+constexpr int kNumThreads = 64;                    // warp-per-row pass: 2 warps per block (fastest of 64, 128, 256)
 constexpr int kNumWarps = kNumThreads / 32;
 constexpr int kNumWarpSlots = 1024;                // (column, value) slots per warp: 8 KB
 constexpr int kNumWarpCap = kNumWarpSlots / 2;     // products per row for the warp path
