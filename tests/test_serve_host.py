@@ -192,3 +192,52 @@ def test_size_classes():
     assert serve._size_class(1) == 1 << 20
     assert serve._size_class((1 << 20) + 1) == 1 << 21
     assert serve._size_class(3 << 20) == 1 << 22
+
+
+class _AutoServer(StubServer):
+    """Every launch completes at the next poll; records whether Python's cyclic
+    collector was on while the loop ran, and can raise from a poll."""
+
+    def __init__(self, raise_at=None):
+        super().__init__(slots=2, budget=100, sizes={"a": 10, "b": 20})
+        self.gc_seen = set()
+        self.polls = 0
+        self.raise_at = raise_at
+
+    def poll(self):
+        import gc
+        self.gc_seen.add(gc.isenabled())
+        self.polls += 1
+        if self.raise_at is not None and self.polls == self.raise_at:
+            raise RuntimeError("poll failed")
+        for ln in self.inflight.values():
+            ln.event.fired = True
+        return super().poll()
+
+
+def test_run_poisson_pauses_the_cyclic_collector_and_restores_it():
+    import gc
+    assert gc.isenabled()
+    srv = _AutoServer()
+    done, _ = serve.run_poisson(srv, [("a", "a"), ("b", "b")], rate=0, n_requests=20, seed=3)
+    assert len(done) == 20 and [r.index for r in done] == list(range(20))
+    assert srv.gc_seen == {False}  # off while serving
+    assert gc.isenabled()          # on again afterwards
+    srv = _AutoServer()
+    serve.run_poisson(srv, [("a", "a")], rate=0, n_requests=5, pause_gc=False)
+    assert srv.gc_seen == {True} and gc.isenabled()
+
+
+def test_run_poisson_restores_the_collector_when_the_loop_raises():
+    import gc
+    srv = _AutoServer(raise_at=1)
+    with pytest.raises(RuntimeError):
+        serve.run_poisson(srv, [("a", "a")], rate=0, n_requests=10)
+    assert gc.isenabled()
+    # a caller that had switched the collector off keeps it off
+    gc.disable()
+    try:
+        serve.run_poisson(_AutoServer(), [("a", "a")], rate=0, n_requests=3)
+        assert not gc.isenabled()
+    finally:
+        gc.enable()
