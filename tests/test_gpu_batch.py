@@ -103,14 +103,36 @@ def _edge_cases():
     ]
 
 
-def test_batch_edge_cases_match_oracle():
+@pytest.mark.parametrize("launches", [1, 4])
+def test_batch_edge_cases_match_oracle(launches):
+    # empty A, an empty sample, the paper's draws, ... in both forms (the
+    # single launch's grid barriers also pass with no work in a phase)
     cases = _edge_cases()
-    batch = sp.Batch(_device_cases(cases), want_flop=True)
+    batch = sp.Batch(_device_cases(cases), want_flop=True, tuning_=sp.tuning(launches=launches))
     batch.run()
     for c, g in zip(cases, _batch_outputs(batch)):
         o = oracle_predict(c["A"], c["B"], c["mode"], c["seed"], c["threshold"], c["sample_num"])
         assert_prediction_equal(g, o, c["name"])
 
+
+
+@pytest.mark.parametrize("launches", [1, 4])
+def test_batch_with_phases_that_have_no_work(launches):
+    # a batch of one 0 x 0 A (no rows, no B rows: no table, sample or heavy
+    # work, one FLOP tile that writes offsets[0]), and the same with a case
+    # whose sample is empty: every phase that has nothing to do must still
+    # pass its barrier and leave exact results
+    none = W.CSR(0, 0, np.zeros(1, np.int32), np.zeros(0, np.int32))
+    b5 = W.CSR(0, 5, np.zeros(1, np.int32), np.zeros(0, np.int32))
+    er = W.erdos_renyi(100, 2, 3)
+    for cases in ([dict(_case(none, b5, seed=1), name="0x0")],
+                  [dict(_case(none, b5, seed=1), name="0x0"), dict(_case(er, er, threshold=0, seed=2), name="no-sample")]):
+        batch = sp.Batch(_device_cases(cases), want_flop=True, tuning_=sp.tuning(launches=launches))
+        for _ in range(2):  # twice: the first run leaves the workspace clean for the next
+            batch.run()
+            for c, g in zip(cases, _batch_outputs(batch)):
+                o = oracle_predict(c["A"], c["B"], c["mode"], c["seed"], c["threshold"], c["sample_num"])
+                assert_prediction_equal(g, o, c["name"])
 
 def test_batch_split_rows_match_oracle():
     # sampled hub rows of 1.3-1.5 M products (a whole block each, over B's
