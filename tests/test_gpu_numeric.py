@@ -49,6 +49,27 @@ def _hub_pair(seed):
     return A, B
 
 
+def _entry_counts(seed):
+    """Rows of 0 to 170 entries (31, 32, 33, 63, 64, 65 among them) over B rows
+    of 1-3 columns: every row has at most 510 products, so every row takes the
+    warp path, which keeps a row's first 32 entries from its FLOP loop and
+    reads the later ones again."""
+    rng = np.random.default_rng(seed)
+    K, N = 3000, 5000
+    rb, cb = [], []
+    for k in range(K):
+        n = int(rng.integers(1, 4))
+        rb += [k] * n
+        cb += rng.choice(N, size=n, replace=False).tolist()
+    B = W.from_coo(K, N, rb, cb)
+    counts = [0, 1, 31, 32, 33, 63, 64, 65, 96, 100, 150, 170] * 20
+    ra, ca = [], []
+    for i, e in enumerate(counts):
+        ra += [i] * e
+        ca += rng.choice(K, size=e, replace=False).tolist()
+    return W.from_coo(len(counts), K, ra, ca), B
+
+
 def _cases():
     er = W.erdos_renyi(1 << 14, 16, 11)
     return {
@@ -62,6 +83,7 @@ def _cases():
         "rect-er": (W.keep_left_columns(W.erdos_renyi(8192, 12, 15), 4096),
                     W.keep_top_rows(W.erdos_renyi(8192, 12, 16), 4096)),
         "hubs": _hub_pair(17),
+        "entry-counts": _entry_counts(18),
     }
 
 
